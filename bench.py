@@ -1,0 +1,288 @@
+#!/usr/bin/env python3
+"""Benchmark: full permeability tensor of a 256^3 consolidated sphere pack.
+
+Workload (one "step"): the whole hot path on one synthetic geometry -- mask upload
+and neighbourhood evaluation, the three drive directions batched in every sweep
+launch, pseudo-time iteration to the window criterion, FP64 reductions, Darcy
+evaluation of the nine k_ij and symmetrisation.  Geometry: 256^3 periodic random
+sequential addition pack of spheres with lognormal radii (median 10 voxels, sigma
+0.3), dilated to porosity 0.38 (seed 2).
+
+Metric: fluid-voxel updates per second = pore voxels x pseudo-time iterations x
+drives / time, whole job (all ranks).  Also reported: seconds to the full k tensor,
+the sweep kernel's achieved HBM bandwidth against the measured peak, the CPU oracle
+on the host cores, and the end-to-end rate through the C ABI with host buffers.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: one process per GPU under torch.distributed.run; every rank solves its own
+replica (independent problems, no collective on the data path), value = sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "kxyz_256c_rsa_lognormal_phi038"
+SHAPE = (256, 256, 256)
+SEED = 2
+TOL = 1e-6  # window criterion, the paper's eps = delta|q| / |q| < 1e-6 (Sec. 7.1)
+METRIC = "fluid-voxel updates/s"
+UNIT = "voxel-updates/s"
+
+
+def make_mask():
+    from paper_2407_19868_gb300 import geometry as G
+    m, info = G.rsa_sphere_pack(SHAPE, 10.0, 0.3, 4.0, 25.0, 0.38, seed=SEED)
+    return m, info
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=6)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_oracle_rate(mask, n_iter: int):
+    """The oracle as it stands, one drive, n_iter iterations of the same workload."""
+    import oracle
+    dom = oracle.Domain(mask)
+    U, p = dom.zeros()
+    t = time.perf_counter()
+    dom.iterate(U, p, n_iter, drive_dir=0)
+    dt = time.perf_counter() - t
+    n_fluid = int(np.count_nonzero(mask == 0))
+    return n_fluid * n_iter / dt, oracle.num_threads(), dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    mask, _ = make_mask()
+    import oracle
+    oracle.build()
+    n_fluid = int(np.count_nonzero(mask == 0))
+    n_iter = args.ref_iters
+    dom = oracle.Domain(mask)
+    rates = []
+    total_t = 0.0
+    for step in range(args.warmup + args.steps):
+        U, p = dom.zeros()
+        t = time.perf_counter()
+        dom.iterate(U, p, n_iter, drive_dir=step % 3)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            rates.append(n_fluid * n_iter / dt)
+            total_t += dt
+    value = n_fluid * n_iter * args.steps / total_t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "shape": list(SHAPE), "porosity": 0.38, "seed": SEED,
+                       "step": f"{n_iter} oracle iterations of one drive (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{n_iter} FP64 oracle iterations per step on the 256^3 mask"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2407_19868_gb300 import api
+
+    api.load()
+    mask, info = make_mask()
+    n_fluid = int(np.count_nonzero(mask == 0))
+    N = mask.size
+    dmask = torch.from_numpy(mask).cuda()
+    opts = dict(tol=args.tol, precision=args.precision, check_every=args.check_every)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        r = api.permeability_tensor(dmask, **opts)
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            results.append(api.permeability_tensor(dmask, **opts))
+        e1.record(stream)
+        barrier()
+    dev_ms = e0.elapsed_time(e1)
+    iters = [r["stats"][0]["iters"] for r in results]
+    updates = sum(n_fluid * it * 3 for it in iters)
+    t_max = dev_ms / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_max, float(updates)], dtype=torch.float64, device="cuda")
+        tt = torch.tensor([t_max], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        t_max, updates = float(tt.item()), float(u.item())
+    value = updates / t_max
+
+    # end to end through the C ABI with host buffers (mask in host memory, k back to host)
+    e2e_value = None
+    if args.e2e_steps > 0:
+        barrier()
+        t = time.perf_counter()
+        e2e_upd = 0
+        for _ in range(args.e2e_steps):
+            r = api.permeability_tensor(mask, **opts)
+            e2e_upd += n_fluid * r["stats"][0]["iters"] * 3
+        torch.cuda.synchronize()
+        e2e_t = time.perf_counter() - t
+        e2e_value = e2e_upd * ws / e2e_t
+
+    # roofline of the dominant kernel (the fused sweep over the 3 drives)
+    sweep_ms = statistics.mean(r["stats"][0]["sweep_ms"] for r in results)
+    alg_bytes = 3 * 32 * N + N / 8  # u_x,u_y,u_z,p read + write, FP32, 3 drives; mask bits
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    kernel_launches = sum(it + (it - 1) // (args.check_every + args.check_every % 2) + 3 for it in iters)
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_iters > 0:
+        rate, cores, secs = cpu_oracle_rate(mask, args.cpu_iters)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_iters} FP64 oracle iterations of drive x on the same 256^3 mask "
+                         f"({secs:.1f} s)"}
+    k = results[-1]["k"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": list(SHAPE), "porosity": round(1 - mask.mean(), 6),
+                   "seed": SEED, "drives": 3, "precision": args.precision, "tol": args.tol,
+                   "check_every": args.check_every, "iters_per_step": iters,
+                   "seconds_to_k_tensor": dev_ms / 1e3 / args.steps,
+                   "l2": "working set 1.6 GB of fields per sweep > 129 MB L2 (no flush needed)",
+                   "parallelism": f"replicas x{ws}"},
+        "k_tensor": [[float(v) for v in row] for row in k],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "fused pseudo-time sweep (3 drives per launch)",
+                     "sweep_ms": sweep_ms, "alg_bytes_per_launch": alg_bytes},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N), "d2h_bytes_per_step": 9 * 8 * 2},
+        "gpu_launches": kernel_launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tol", type=float, default=TOL)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "dc64", "fp64"])
+    ap.add_argument("--check-every", type=int, default=200)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=30)
+    ap.add_argument("--ref-iters", type=int, default=5)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

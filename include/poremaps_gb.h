@@ -1,0 +1,169 @@
+/*
+ * poremaps_gb.h - C ABI of the GB300 permeability solver (libpm_gb300.so).
+ *
+ * The library computes the intrinsic permeability tensor k of a binary voxel image by
+ * the method of Krach, Ruf and Steeb, "POREMAPS: A finite difference based Porous Media
+ * Anisotropic Permeability Solver for Stokes flow" (arXiv 2407.19868):
+ *   - pseudo-unsteady (artificial compressibility) Stokes equations, Sec. 3 and
+ *     Appendix A, stepped in pseudo time on a staggered MAC grid, Sec. 4 "Grid";
+ *   - no-slip / no-penetration at the voxel faces between pore and solid through the
+ *     Taylor-series wall cases of Sec. 4 and Appendix B; periodic outer boundaries
+ *     (or no-slip walls), Sec. 4 "Boundary ...";
+ *   - per iteration the velocity update, then the pressure update with the new
+ *     velocities, then the evaluation of permeability and convergence (Algorithm 1);
+ *   - k from Darcy's law with one drive per axis, Eq. (darcy), Eq. (cases_pressure)
+ *     and Appendix C, off-diagonals averaged (Sec. 6.4, Appendix C).
+ *
+ * Conventions used by every entry point
+ *   - Masks are uint8 arrays in C order [nz][ny][nx] (x fastest); nonzero = solid.
+ *   - Fields are structure-of-arrays: u = [u_x | u_y | u_z], each nx*ny*nz long, u_d(c)
+ *     lives on the +d face of cell c; p lives at cell centres.  Non-fluid faces hold 0.
+ *   - Fields passed to or returned by pm_iterate are in the paper's iteration units
+ *     (Sec. 4: length 1 voxel, velocity 1 voxel/s, Re and c*^2 from pm_options); the
+ *     drive is a body force f on the fluid faces normal to the drive axis, which is the
+ *     same discrete problem as the paper's pressure gradient with a periodic jump.
+ *   - pm_solve_direction returns Darcy-scaled fields: u in the units of
+ *     drive * voxel_size^2 / viscosity (m/s for SI inputs), p in drive * voxel_size.
+ *   - k is returned in voxel_size^2 units (m^2 for voxel_size in metres).
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream).  The library runs
+ *     on its own internal stream ordered after cuda_stream and orders cuda_stream after
+ *     its work; device outputs are complete on cuda_stream when the call returns.
+ *   - Ownership: the caller owns every pointer it passes and keeps device pointers valid
+ *     for the call; the library never frees caller memory.  Scratch (ping-pong fields,
+ *     neighbourhood flags, FP64 master copies, reduction buffers) is allocated with
+ *     cudaMallocAsync inside each call and released before it returns.
+ *   - Errors: every function returns a pm_status; nothing throws or aborts.  On an error
+ *     return, outputs may be partially written.
+ */
+#ifndef POREMAPS_GB_H
+#define POREMAPS_GB_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PM_API __attribute__((visibility("default")))
+#else
+#define PM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pm_status {
+    PM_OK = 0,
+    PM_ERR_INVALID_ARG = 1,     /* NULL pointer, bad enum, dims < 1, bad option */
+    PM_ERR_NO_FLUID = 2,        /* the mask has no pore voxel */
+    PM_ERR_NOT_PERCOLATING = 3, /* no fluid path wraps the domain along a drive axis;
+                                   that k column is 0, the others are still computed */
+    PM_ERR_NOT_CONVERGED = 4,   /* max_iter reached; outputs valid, stats say how far */
+    PM_ERR_DIVERGED = 5,        /* NaN or Inf in the reductions */
+    PM_ERR_OOM = 6,             /* device allocation failed */
+    PM_ERR_CUDA = 7,            /* any other CUDA runtime error */
+    PM_ERR_TIMEOUT = 8,         /* a bounded device wait ran out */
+    PM_ERR_UNSUPPORTED = 9      /* option combination not implemented */
+} pm_status;
+
+enum { PM_BC_PERIODIC = 0, PM_BC_WALL = 1 };
+
+/* Arithmetic of the pseudo-time sweeps. */
+enum {
+    PM_FP32_RED64 = 0, /* FP32 fields, FP64 reductions (mean velocity, residual) */
+    PM_FP32_DC64 = 1,  /* as above, then FP64 defect correction: r = b - K x in FP64,
+                          K d = r by FP32 sweeps, x += d, until the tolerance holds */
+    PM_FP64 = 2        /* FP64 fields throughout */
+};
+
+typedef struct pm_domain {
+    int32_t nx, ny, nz;       /* voxels per axis, each >= 1 */
+    const uint8_t *mask;      /* [nz][ny][nx], nonzero = solid; host or device */
+    int32_t mask_on_device;   /* 1: mask is a device pointer */
+    double voxel_size;        /* dx; k is returned in dx^2 units (m^2 if dx in m) */
+    double viscosity;         /* mu; scales the returned velocities only */
+    int32_t bc[3];            /* per axis x, y, z: PM_BC_PERIODIC or PM_BC_WALL */
+} pm_domain;
+
+typedef struct pm_options {
+    double tol;               /* stop when the mean velocity changed by less than tol
+                                 (relative to the driven component) over one window,
+                                 both measured and extrapolated (geometric tail) */
+    int32_t check_every;      /* window length M in sweeps (rounded up to even) */
+    int64_t max_iter;         /* sweep limit per drive */
+    int32_t precision;        /* PM_FP32_RED64, PM_FP32_DC64 or PM_FP64 */
+    double dt_safety;         /* pseudo-time step = dt_safety x stability root (0.9) */
+    double Re;                /* Reynolds number (Sec. 4: 0.01) */
+    double c2;                /* squared artificial speed of sound (Sec. 4: 1.5e6) */
+    int32_t use_graph;        /* 1: replay each window as a captured CUDA graph */
+    int32_t check_percolation;/* 1: host breadth-first search before solving */
+    double dc_switch_tol;     /* PM_FP32_DC64: leave plain FP32 sweeps at this change */
+    int32_t dc_max_rounds;    /* PM_FP32_DC64: maximum correction rounds */
+    int32_t kernel;           /* 0 = default sweep kernel, 1 = simple reference kernel */
+    int32_t reserved[8];
+} pm_options;
+
+typedef struct pm_stats {
+    int64_t iters;            /* pseudo-time iterations taken */
+    double q[3];              /* mean velocity q_d (iteration units) at the end */
+    double delta;             /* last window's relative change */
+    double err_est;           /* extrapolated remaining change */
+    double div_res;           /* L2 norm of the discrete divergence (iteration units) */
+    double seconds;           /* wall time of the call */
+    double sweep_ms;          /* CUDA-event time per sweep launch (mean over windows) */
+    int64_t sweeps_timed;     /* sweeps inside the timed windows */
+    int32_t dc_rounds;        /* defect-correction rounds done */
+    int32_t status;           /* pm_status of this drive */
+    int32_t percolates;       /* 1 if a fluid path wraps the domain along the drive */
+    int32_t reserved[5];
+} pm_stats;
+
+/* Fills *opt with the defaults: tol 1e-6, check_every 200, max_iter 2e6,
+ * PM_FP32_RED64, dt_safety 0.9, Re 0.01, c2 1.5e6, graphs on, percolation check on,
+ * dc_switch_tol 1e-5, dc_max_rounds 8. */
+PM_API void pm_default_options(pm_options *opt);
+
+/* Human-readable text of a pm_status (static storage). */
+PM_API const char *pm_strerror(int status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+PM_API int pm_version(void);
+
+/* Pseudo-time step used for given options (the paper does not state one): dt_safety x
+ * the positive root of 12 c2 dt^2 + 40 dt / Re - 4 = 0. */
+PM_API double pm_time_step(const pm_options *opt);
+
+/* Advance n pseudo-time iterations of Algorithm 1 in place, paper order (velocity update
+ * from the old state, then pressure update with the new velocities), drive = body force
+ * f on the fluid faces normal to axis dir (iteration units, Sec. 4).
+ *   u: device, 3*N values, p: device, N values; float for PM_FP32_*, double for PM_FP64.
+ *   Values on non-fluid faces / solid cells are set to 0 on entry.
+ *   Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA. */
+PM_API int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_options *opt, int64_t n,
+               void *u, void *p, void *cuda_stream);
+
+/* One drive direction to convergence (Algorithm 1, Sec. 4 "Permeability computation").
+ *   dir: 0, 1, 2 = drive along e_1, e_2, e_3 (case a, b, c of Eq. cases_pressure).
+ *   drive: |h| (pressure gradient magnitude, e.g. Pa/m); scales the returned fields.
+ *   u (device, 3N floats) / p (device, N floats): Darcy-scaled fields out, or NULL.
+ *   u0 / p0 (device, same layout and units as u / p): warm start, or NULL for zero.
+ *   k_col (host, 3 doubles, may be NULL): column dir of k (Appendix C), dx^2 units.
+ *   st (host, may be NULL): statistics.
+ *   Errors: PM_ERR_INVALID_ARG, PM_ERR_NO_FLUID, PM_ERR_NOT_PERCOLATING (k_col = 0),
+ *   PM_ERR_NOT_CONVERGED, PM_ERR_DIVERGED, PM_ERR_OOM, PM_ERR_CUDA. */
+PM_API int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_options *opt,
+                       float *u, float *p, const float *u0, const float *p0, double *k_col,
+                       pm_stats *st, void *cuda_stream);
+
+/* Full tensor: the three drives of Eq. (cases_pressure) solved together, batched in each
+ * sweep launch over the shared mask; k from the nine Darcy equations of Appendix C.
+ *   k_out (host, 9 doubles, row-major): symmetrised k_ij = (k_ij + k_ji) / 2.
+ *   k_raw (host, 9 doubles or NULL): column j from drive j before averaging.
+ *   st (host, 3 entries or NULL): per drive statistics.
+ *   A non-percolating axis gives a zero row and column and PM_ERR_NOT_PERCOLATING.
+ *   Other errors as pm_solve_direction. */
+PM_API int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_options *opt,
+                           double k_out[9], double k_raw[9], pm_stats st[3], void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POREMAPS_GB_H */

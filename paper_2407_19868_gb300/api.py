@@ -1,0 +1,224 @@
+"""Python binding of the GB300 permeability solver's C ABI (``include/poremaps_gb.h``).
+
+Argument marshalling only: every step of the solve runs in ``libpm_gb300.so``.
+PyTorch supplies device memory and the current CUDA stream.  If the library has not
+been built, :func:`load` raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PM_OK = 0
+PM_ERR_INVALID_ARG = 1
+PM_ERR_NO_FLUID = 2
+PM_ERR_NOT_PERCOLATING = 3
+PM_ERR_NOT_CONVERGED = 4
+PM_ERR_DIVERGED = 5
+PM_ERR_OOM = 6
+PM_ERR_CUDA = 7
+PM_ERR_TIMEOUT = 8
+PM_ERR_UNSUPPORTED = 9
+
+PERIODIC = 0
+WALL = 1
+
+FP32_RED64 = 0
+FP32_DC64 = 1
+FP64 = 2
+_PRECISION = {"fp32": FP32_RED64, "fp32_red64": FP32_RED64, "fp32_dc64": FP32_DC64, "dc64": FP32_DC64,
+              "fp64": FP64}
+
+# every function the header declares (checked by the ABI test)
+EXPORTED = ["pm_default_options", "pm_strerror", "pm_version", "pm_time_step", "pm_iterate",
+            "pm_solve_direction", "pm_permeability_tensor"]
+
+
+class PMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {strerror(status)} (status {status})")
+        self.status = status
+
+
+class Domain(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("mask", C.c_void_p),
+                ("mask_on_device", C.c_int32), ("voxel_size", C.c_double), ("viscosity", C.c_double),
+                ("bc", C.c_int32 * 3)]
+
+
+class Options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("check_every", C.c_int32), ("max_iter", C.c_int64),
+                ("precision", C.c_int32), ("dt_safety", C.c_double), ("Re", C.c_double),
+                ("c2", C.c_double), ("use_graph", C.c_int32), ("check_percolation", C.c_int32),
+                ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
+                ("reserved", C.c_int32 * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("q", C.c_double * 3), ("delta", C.c_double),
+                ("err_est", C.c_double), ("div_res", C.c_double), ("seconds", C.c_double),
+                ("sweep_ms", C.c_double), ("sweeps_timed", C.c_int64), ("dc_rounds", C.c_int32),
+                ("status", C.c_int32), ("percolates", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+    def as_dict(self):
+        return {"iters": int(self.iters), "q": [float(v) for v in self.q], "delta": float(self.delta),
+                "err_est": float(self.err_est), "div_res": float(self.div_res),
+                "seconds": float(self.seconds), "sweep_ms": float(self.sweep_ms),
+                "sweeps_timed": int(self.sweeps_timed), "dc_rounds": int(self.dc_rounds),
+                "status": int(self.status), "percolates": bool(self.percolates)}
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load():
+    """Open libpm_gb300.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(path)
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.pm_default_options.argtypes = [C.POINTER(Options)]
+        L.pm_strerror.restype = C.c_char_p
+        L.pm_strerror.argtypes = [C.c_int]
+        L.pm_version.restype = C.c_int
+        L.pm_time_step.restype = C.c_double
+        L.pm_time_step.argtypes = [C.POINTER(Options)]
+        L.pm_iterate.argtypes = [C.POINTER(Domain), C.c_int, C.c_double, C.POINTER(Options), C.c_int64,
+                                 vp, vp, vp]
+        L.pm_solve_direction.argtypes = [C.POINTER(Domain), C.c_int, C.c_double, C.POINTER(Options),
+                                         vp, vp, vp, vp, dp, C.POINTER(Stats), vp]
+        L.pm_permeability_tensor.argtypes = [C.POINTER(Domain), C.c_double, C.POINTER(Options), dp, dp,
+                                             C.POINTER(Stats), vp]
+        _LIB = L
+        return L
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().pm_strerror(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def options(**kw) -> Options:
+    o = Options()
+    load().pm_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = _PRECISION[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def time_step(**kw) -> float:
+    o = options(**kw)
+    return float(load().pm_time_step(C.byref(o)))
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class _Mask:
+    """Keeps the mask alive and describes it as a pm_domain."""
+
+    def __init__(self, mask, dx=1.0, mu=1.0, bc=(PERIODIC, PERIODIC, PERIODIC)):
+        import torch
+        if isinstance(mask, torch.Tensor):
+            m = mask.contiguous()
+            if m.dtype != torch.uint8:
+                m = (m != 0).to(torch.uint8)
+            self._keep = m
+            ptr, on_dev = m.data_ptr(), int(m.is_cuda)
+            shape = tuple(m.shape)
+        else:
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            self._keep = m
+            ptr, on_dev = m.ctypes.data, 0
+            shape = m.shape
+        if len(shape) != 3:
+            raise ValueError("mask must be 3-D [nz][ny][nx]")
+        nz, ny, nx = shape
+        self.shape = shape
+        self.N = nx * ny * nz
+        self.dom = Domain(nx, ny, nz, ptr, on_dev, float(dx), float(mu), (C.c_int32 * 3)(*bc))
+
+
+def _check(status: int, what: str, soft=(PM_OK,)):
+    if status not in soft:
+        raise PMError(status, what)
+    return status
+
+
+def iterate(mask, u, p, n: int, drive_dir: int = 0, drive: float = 1.0, bc=(0, 0, 0), stream=None, **opts):
+    """Algorithm 1 loop body n times in place on device fields (iteration units):
+    u: (3, nz, ny, nx), p: (nz, ny, nx), float32 (precision fp32) or float64 (fp64)."""
+    import torch
+    m = _Mask(mask, bc=bc)
+    prec = opts.pop("precision", "fp64" if u.dtype == torch.float64 else "fp32")
+    o = options(precision=prec, **opts)
+    want = torch.float64 if o.precision == FP64 else torch.float32
+    if u.dtype != want or p.dtype != want or not (u.is_cuda and p.is_cuda):
+        raise TypeError("u, p must be CUDA tensors of the precision's type")
+    if not (u.is_contiguous() and p.is_contiguous()) or u.numel() != 3 * m.N or p.numel() != m.N:
+        raise ValueError("u, p must be contiguous with 3N and N elements")
+    st = load().pm_iterate(C.byref(m.dom), int(drive_dir), float(drive), C.byref(o), int(n),
+                           u.data_ptr(), p.data_ptr(), _stream(stream))
+    _check(st, "pm_iterate")
+    return u, p
+
+
+def solve_direction(mask, drive_dir: int, drive: float = 1.0, dx: float = 1.0, mu: float = 1.0,
+                    bc=(0, 0, 0), fields: bool = True, u0=None, p0=None, stream=None, **opts):
+    """One drive direction to convergence.  Returns dict(k_col, u, p, stats, status);
+    u, p are Darcy-scaled float32 CUDA tensors (None unless ``fields``)."""
+    import torch
+    m = _Mask(mask, dx=dx, mu=mu, bc=bc)
+    o = options(**opts)
+    dev = torch.device("cuda")
+    u = torch.empty((3,) + m.shape, dtype=torch.float32, device=dev) if fields else None
+    p = torch.empty(m.shape, dtype=torch.float32, device=dev) if fields else None
+    k = (C.c_double * 3)()
+    s = Stats()
+    st = load().pm_solve_direction(C.byref(m.dom), int(drive_dir), float(drive), C.byref(o),
+                                   u.data_ptr() if u is not None else None,
+                                   p.data_ptr() if p is not None else None,
+                                   u0.data_ptr() if u0 is not None else None,
+                                   p0.data_ptr() if p0 is not None else None,
+                                   k, C.byref(s), _stream(stream))
+    _check(st, "pm_solve_direction", soft=(PM_OK, PM_ERR_NOT_PERCOLATING, PM_ERR_NOT_CONVERGED))
+    return {"k_col": np.array(k[:]), "u": u, "p": p, "stats": s.as_dict(), "status": st}
+
+
+def permeability_tensor(mask, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts):
+    """Full tensor, three drives batched per sweep launch.  Returns
+    dict(k (symmetrised 3x3), k_raw, stats (3 dicts), status)."""
+    m = _Mask(mask, dx=dx, bc=bc)
+    o = options(**opts)
+    k = (C.c_double * 9)()
+    kr = (C.c_double * 9)()
+    s = (Stats * 3)()
+    st = load().pm_permeability_tensor(C.byref(m.dom), 1.0, C.byref(o), k, kr, s, _stream(stream))
+    _check(st, "pm_permeability_tensor", soft=(PM_OK, PM_ERR_NOT_PERCOLATING, PM_ERR_NOT_CONVERGED))
+    return {"k": np.array(k[:]).reshape(3, 3), "k_raw": np.array(kr[:]).reshape(3, 3),
+            "stats": [s[i].as_dict() for i in range(3)], "status": st}

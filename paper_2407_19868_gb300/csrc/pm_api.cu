@@ -1,0 +1,739 @@
+// Host driver and C ABI of the GB300 permeability solver (see include/poremaps_gb.h).
+//
+// Call flow of a solve (Algorithm 1 of the paper, one GPU, no halo exchange):
+//   mask -> device -> neighbourhood flags (classify_kernel)
+//   -> percolation check (host breadth-first search, Sec. 5.1 assumes percolation)
+//   -> first sweep (velocity of iteration 1)
+//   -> windows of M fused sweeps, the last one with FP64 block sums, captured once as a
+//      CUDA graph and replayed; after each window 4 doubles per drive come back to the
+//      host for the convergence criterion (the only host<->device traffic in the loop)
+//   -> last half sweep (pressure of the last iteration)
+//   -> optional FP64 defect correction -> Darcy (Appendix C) -> symmetrise.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/poremaps_gb.h"
+#include "pm_kernels.cuh"
+#include "pm_sweep_tiled.cuh"
+
+using namespace pmgb;
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+
+struct Status {
+    int code = PM_OK;
+};
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PM_OK;
+    if (e == cudaErrorMemoryAllocation) return PM_ERR_OOM;
+    return PM_ERR_CUDA;
+}
+
+#define PM_CK(call)                                      \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) {                         \
+            (void)cudaGetLastError();                    \
+            return map_cuda(e_);                         \
+        }                                                \
+    } while (0)
+
+// Stream-ordered scratch that is released when the owner goes out of scope.
+struct Scratch {
+    cudaStream_t s = nullptr;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    int alloc(T **p, size_t count) {
+        void *v = nullptr;
+        cudaError_t e = cudaMallocAsync(&v, count * sizeof(T) + 16, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *p = nullptr;
+            return map_cuda(e);
+        }
+        ptrs.push_back(v);
+        *p = static_cast<T *>(v);
+        return PM_OK;
+    }
+};
+
+// Internal stream ordered after the caller's stream; at destruction the caller's stream
+// is ordered after all internal work.
+struct StreamScope {
+    cudaStream_t user = nullptr, s = nullptr;
+    cudaEvent_t ev = nullptr;
+    int status = PM_OK;
+    explicit StreamScope(void *user_stream) : user(static_cast<cudaStream_t>(user_stream)) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, user);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            status = map_cuda(e);
+        }
+    }
+    ~StreamScope() {
+        if (s) {
+            if (ev) {
+                cudaEventRecord(ev, s);
+                cudaStreamWaitEvent(user, ev, 0);
+            }
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+int launch_grid(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
+}
+
+// ------------------------------------------------------------------ geometry
+struct Geometry {
+    int nx = 0, ny = 0, nz = 0;
+    int per[3] = {1, 1, 1};
+    long long N = 0;
+    uint8_t *flags = nullptr;  // device
+    long long n_fluid_cells = 0;
+};
+
+int validate_domain(const pm_domain *dom) {
+    if (!dom || !dom->mask) return PM_ERR_INVALID_ARG;
+    if (dom->nx < 1 || dom->ny < 1 || dom->nz < 1) return PM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (dom->bc[a] != PM_BC_PERIODIC && dom->bc[a] != PM_BC_WALL) return PM_ERR_INVALID_ARG;
+    if (!(dom->voxel_size > 0) || !(dom->viscosity > 0)) return PM_ERR_INVALID_ARG;
+    return PM_OK;
+}
+
+int validate_options(const pm_options *o) {
+    if (!o) return PM_ERR_INVALID_ARG;
+    if (!(o->tol > 0) || o->check_every < 1 || o->max_iter < 1) return PM_ERR_INVALID_ARG;
+    if (o->precision < PM_FP32_RED64 || o->precision > PM_FP64) return PM_ERR_INVALID_ARG;
+    if (!(o->dt_safety > 0) || !(o->Re > 0) || !(o->c2 > 0)) return PM_ERR_INVALID_ARG;
+    return PM_OK;
+}
+
+// Host copy of the mask (needed by the percolation search).
+int host_mask(const pm_domain *dom, std::vector<uint8_t> &out) {
+    size_t N = (size_t)dom->nx * dom->ny * dom->nz;
+    out.resize(N);
+    if (dom->mask_on_device) {
+        PM_CK(cudaMemcpy(out.data(), dom->mask, N, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(out.data(), dom->mask, N);
+    }
+    return PM_OK;
+}
+
+int build_geometry(const pm_domain *dom, cudaStream_t s, Scratch &scr, Geometry &g) {
+    g.nx = dom->nx;
+    g.ny = dom->ny;
+    g.nz = dom->nz;
+    for (int a = 0; a < 3; ++a) g.per[a] = dom->bc[a] == PM_BC_PERIODIC;
+    g.N = (long long)g.nx * g.ny * g.nz;
+    int st = scr.alloc(&g.flags, (size_t)g.N);
+    if (st) return st;
+    const uint8_t *dmask = dom->mask;
+    if (!dom->mask_on_device) {
+        uint8_t *m = nullptr;
+        if ((st = scr.alloc(&m, (size_t)g.N))) return st;
+        PM_CK(cudaMemcpyAsync(m, dom->mask, (size_t)g.N, cudaMemcpyHostToDevice, s));
+        dmask = m;
+    }
+    classify_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
+                                                     g.flags);
+    PM_CK(cudaGetLastError());
+    return PM_OK;
+}
+
+// Does a face-connected path of pore cells wrap the periodic domain along each axis?
+// Breadth-first search that carries, per visited cell, how often the path to it crossed
+// each periodic boundary; meeting a visited cell with another crossing count along
+// axis a closes a loop that wraps around a.
+void percolation_host(const std::vector<uint8_t> &mask, int nx, int ny, int nz, const int per[3],
+                      int out[3]) {
+    const long long N = (long long)nx * ny * nz;
+    out[0] = out[1] = out[2] = 0;
+    std::vector<uint8_t> seen((size_t)N, 0);
+    std::vector<int16_t> wind((size_t)N * 3);
+    std::vector<long long> queue;
+    queue.reserve(1 << 16);
+    const int n[3] = {nx, ny, nz};
+    for (long long s0 = 0; s0 < N; ++s0) {
+        if (mask[s0] || seen[s0]) continue;
+        queue.clear();
+        queue.push_back(s0);
+        seen[s0] = 1;
+        wind[s0 * 3] = wind[s0 * 3 + 1] = wind[s0 * 3 + 2] = 0;
+        for (size_t h = 0; h < queue.size(); ++h) {
+            long long c = queue[h];
+            int co[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+            for (int a = 0; a < 3; ++a)
+                for (int m = -1; m <= 1; m += 2) {
+                    int cc[3] = {co[0], co[1], co[2]};
+                    int w = 0;
+                    cc[a] += m;
+                    if (cc[a] < 0 || cc[a] >= n[a]) {
+                        if (!per[a]) continue;
+                        w = cc[a] < 0 ? -1 : 1;
+                        cc[a] = (cc[a] + n[a]) % n[a];
+                    }
+                    long long b = cc[0] + (long long)nx * (cc[1] + (long long)ny * cc[2]);
+                    if (mask[b]) continue;
+                    int16_t wn[3] = {wind[c * 3], wind[c * 3 + 1], wind[c * 3 + 2]};
+                    wn[a] = (int16_t)(wn[a] + w);
+                    if (!seen[b]) {
+                        seen[b] = 1;
+                        for (int k = 0; k < 3; ++k) wind[b * 3 + k] = wn[k];
+                        queue.push_back(b);
+                    } else {
+                        for (int k = 0; k < 3; ++k)
+                            if (wind[b * 3 + k] != wn[k]) out[k] = 1;
+                    }
+                }
+        }
+    }
+}
+
+double time_step(const pm_options *o) {
+    // 12 c2 dt^2 + (40 / Re) dt - 4 = 0: acoustic bound of the velocity-then-pressure
+    // update (cell Laplacian eigenvalues <= 12) plus the viscous Gershgorin bound
+    // (<= 20 / Re) of the explicit velocity update
+    const double a = 12.0 * o->c2, b = 40.0 / o->Re, c = -4.0;
+    return o->dt_safety * (-b + std::sqrt(b * b - 4.0 * a * c)) / (2.0 * a);
+}
+
+// ------------------------------------------------------------------ solver state
+template <typename T>
+struct Fields {
+    T *u[2] = {nullptr, nullptr};
+    T *p[2] = {nullptr, nullptr};
+    int cur = 0;  // buffer holding the latest state
+};
+
+template <typename T>
+struct Solver {
+    const Geometry &g;
+    const pm_options &o;
+    cudaStream_t s;
+    Scratch &scr;
+    int nprob = 0;
+    Fields<T> F[kMaxBatch];
+    int dir[kMaxBatch] = {0, 0, 0, 0};
+    double force[kMaxBatch] = {0, 0, 0, 0};
+    const T *src[kMaxBatch] = {nullptr, nullptr, nullptr, nullptr};
+    double *partials = nullptr;  // [nprob][nblk][4]
+    double *dq = nullptr;        // [nprob][4]
+    double *hq = nullptr;        // pinned [nprob][4]
+    long long nblk = 0;
+    T dt = 0, dtc2 = 0, inv_re = 0;
+    const T *alpha = nullptr;
+
+    Solver(const Geometry &gg, const pm_options &oo, cudaStream_t ss, Scratch &sc)
+        : g(gg), o(oo), s(ss), scr(sc) {}
+    ~Solver() {
+        if (hq) cudaFreeHost(hq);
+    }
+
+    dim3 block() const { return dim3(32, 8, 1); }
+    dim3 grid() const { return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)(g.nz * nprob)); }
+
+    int init(int np) {
+        nprob = np;
+        const double dts = time_step(&o);
+        dt = (T)dts;
+        dtc2 = (T)(dts * o.c2);
+        inv_re = (T)(1.0 / o.Re);
+        dim3 gr = grid();
+        nblk = (long long)gr.x * gr.y * g.nz;
+        int st;
+        for (int k = 0; k < nprob; ++k) {
+            for (int b = 0; b < 2; ++b) {
+                if ((st = scr.alloc(&F[k].u[b], (size_t)(3 * g.N)))) return st;
+                if ((st = scr.alloc(&F[k].p[b], (size_t)g.N))) return st;
+                PM_CK(cudaMemsetAsync(F[k].u[b], 0, sizeof(T) * 3 * g.N, s));
+                PM_CK(cudaMemsetAsync(F[k].p[b], 0, sizeof(T) * g.N, s));
+            }
+            F[k].cur = 0;
+        }
+        if ((st = scr.alloc(&partials, (size_t)(nprob * nblk * 4)))) return st;
+        if ((st = scr.alloc(&dq, (size_t)(nprob * 4)))) return st;
+        PM_CK(cudaMallocHost(&hq, sizeof(double) * nprob * 4));
+        return PM_OK;
+    }
+
+    // Copy a caller state (same type, iteration units) into the current buffers.
+    int load_state(int k, const T *u, const T *p) {
+        if (u) PM_CK(cudaMemcpyAsync(F[k].u[F[k].cur], u, sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
+        if (p) PM_CK(cudaMemcpyAsync(F[k].p[F[k].cur], p, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, s));
+        sanitize_kernel<T><<<launch_grid(g.N), 256, 0, s>>>(g.flags, g.N, F[k].u[F[k].cur], F[k].p[F[k].cur]);
+        PM_CK(cudaGetLastError());
+        return PM_OK;
+    }
+
+    SweepBatch<T> batch(bool reduce) {
+        SweepBatch<T> B{};
+        B.nx = g.nx;
+        B.ny = g.ny;
+        B.nz = g.nz;
+        for (int a = 0; a < 3; ++a) B.per[a] = g.per[a];
+        B.N = g.N;
+        B.flags = g.flags;
+        B.alpha = alpha;
+        B.inv_re = inv_re;
+        B.dt = dt;
+        B.dtc2 = dtc2;
+        B.nprob = nprob;
+        for (int k = 0; k < nprob; ++k) {
+            SweepProblem<T> &P = B.prob[k];
+            P.uin = F[k].u[F[k].cur];
+            P.pin = F[k].p[F[k].cur];
+            P.uout = F[k].u[1 - F[k].cur];
+            P.pout = F[k].p[1 - F[k].cur];
+            P.src = src[k];
+            for (int d = 0; d < 3; ++d) P.f[d] = (T)(d == dir[k] ? force[k] : 0.0);
+            P.partials = reduce ? partials + (size_t)k * reduce_blocks() * 4 : nullptr;
+        }
+        return B;
+    }
+
+    template <int MODE, bool RED>
+    void launch_simple(const SweepBatch<T> &B, bool has_src) {
+        if (has_src)
+            sweep_simple_kernel<T, MODE, RED, true><<<grid(), block(), 0, s>>>(B);
+        else
+            sweep_simple_kernel<T, MODE, RED, false><<<grid(), block(), 0, s>>>(B);
+    }
+
+    // One sweep of the given mode; flips the ping-pong buffers.
+    int sweep(int mode, bool reduce) {
+        SweepBatch<T> B = batch(reduce);
+        bool has_src = false;
+        for (int k = 0; k < nprob; ++k) has_src |= src[k] != nullptr;
+        const bool tiled = o.kernel == 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
+        if (tiled) {
+            int st = launch_tiled<T>(B, mode, reduce, has_src, s);
+            if (st) return st;
+        } else if (mode == kModeU) {
+            reduce ? launch_simple<kModeU, true>(B, has_src) : launch_simple<kModeU, false>(B, has_src);
+        } else if (mode == kModePU) {
+            reduce ? launch_simple<kModePU, true>(B, has_src) : launch_simple<kModePU, false>(B, has_src);
+        } else {
+            reduce ? launch_simple<kModeP, true>(B, has_src) : launch_simple<kModeP, false>(B, has_src);
+        }
+        PM_CK(cudaGetLastError());
+        for (int k = 0; k < nprob; ++k) F[k].cur ^= 1;
+        return PM_OK;
+    }
+
+    long long reduce_blocks() const {
+        return (o.kernel == 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob)) ? tiled_num_blocks<T>(g.nx, g.ny, g.nz)
+                                                                            : nblk;
+    }
+
+    int reduce_to_host_async() {
+        reduce_partials_kernel<<<nprob, 256, 0, s>>>(partials, reduce_blocks(), g.N, dq);
+        PM_CK(cudaGetLastError());
+        PM_CK(cudaMemcpyAsync(hq, dq, sizeof(double) * nprob * 4, cudaMemcpyDeviceToHost, s));
+        return PM_OK;
+    }
+
+    // Reduction of the current state (a pressure-only pass would change p; instead run
+    // the sums on a copy-free pass: P-mode reads u and writes p of the other buffer).
+    int window(int M) {
+        int st;
+        for (int i = 0; i < M; ++i)
+            if ((st = sweep(kModePU, i == M - 1))) return st;
+        return reduce_to_host_async();
+    }
+};
+
+struct Monitor {
+    double q_prev[3] = {0, 0, 0};
+    double d_prev = -1.0;
+    double delta = INFINITY, err = INFINITY;
+    bool converged = false;
+    // Window criterion (reading of Sec. 7.1, eps = delta|q| / |q|): relative change of
+    // the mean velocity over one window, and its geometric-tail extrapolation.
+    void update(const double q[3], int dir, double tol) {
+        double ref = std::fabs(q[dir]);
+        double ch = 0.0;
+        for (int d = 0; d < 3; ++d) ch = std::fmax(ch, std::fabs(q[d] - q_prev[d]));
+        delta = ref > 0 ? ch / ref : INFINITY;
+        if (ch == 0.0)
+            err = 0.0;
+        else if (d_prev > 0 && delta < d_prev) {
+            double r = delta / d_prev;
+            err = delta * r / (1.0 - r);
+        } else
+            err = INFINITY;
+        d_prev = delta;
+        for (int d = 0; d < 3; ++d) q_prev[d] = q[d];
+        converged = delta < tol && err < tol;
+    }
+};
+
+// Runs the batch to convergence from the loaded state.  Returns a pm_status.
+template <typename T>
+int run_to_convergence(Solver<T> &S, pm_stats *st, double t0) {
+    const pm_options &o = S.o;
+    int M = o.check_every + (o.check_every & 1);
+    Monitor mon[kMaxBatch];
+    int status = PM_OK;
+    long long iters = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double win_ms = 0.0;
+    long long win_sweeps = 0;
+    PM_CK(cudaEventCreate(&e0));
+    PM_CK(cudaEventCreate(&e1));
+    int rc = S.sweep(kModeU, false);
+    if (rc) status = rc;
+    iters = 1;
+    bool done = status != PM_OK;
+    bool use_graph = o.use_graph != 0;
+    if (!done && use_graph) {
+        // capture one window; M is even so the ping-pong roles repeat
+        const int cur0 = S.F[0].cur;
+        cudaError_t e = cudaStreamBeginCapture(S.s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = S.window(M);
+            e = cudaStreamEndCapture(S.s, &graph);
+            if (rc == PM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess || rc != PM_OK) {
+                (void)cudaGetLastError();
+                use_graph = false;
+                if (exec) cudaGraphExecDestroy(exec);
+                exec = nullptr;
+            }
+        } else {
+            (void)cudaGetLastError();
+            use_graph = false;
+        }
+        for (int k = 0; k < S.nprob; ++k) S.F[k].cur = cur0;
+    }
+    while (!done) {
+        cudaEventRecord(e0, S.s);
+        if (use_graph) {
+            cudaError_t e = cudaGraphLaunch(exec, S.s);
+            if (e != cudaSuccess) {
+                status = map_cuda(e);
+                break;
+            }
+        } else if ((rc = S.window(M))) {
+            status = rc;
+            break;
+        }
+        cudaEventRecord(e1, S.s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            status = map_cuda(e);
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        win_ms += ms;
+        win_sweeps += M;
+        iters += M;
+        bool all = true, bad = false;
+        for (int k = 0; k < S.nprob; ++k) {
+            const double *q = S.hq + 4 * k;
+            if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) || !std::isfinite(q[3]))
+                bad = true;
+            mon[k].update(q, S.dir[k], o.tol);
+            all = all && mon[k].converged;
+            if (st) {
+                st[k].div_res = std::sqrt(q[3]);
+                for (int d = 0; d < 3; ++d) st[k].q[d] = q[d];
+            }
+        }
+        if (bad) {
+            status = PM_ERR_DIVERGED;
+            break;
+        }
+        if (all) break;
+        if (iters >= o.max_iter) {
+            status = PM_ERR_NOT_CONVERGED;
+            break;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    // last half step: pressure of the last iteration, plus the sums of the final state
+    if (status == PM_OK || status == PM_ERR_NOT_CONVERGED) {
+        if ((rc = S.sweep(kModeP, true)) || (rc = S.reduce_to_host_async())) status = rc;
+        else {
+            cudaError_t e = cudaStreamSynchronize(S.s);
+            if (e != cudaSuccess) status = map_cuda(e);
+        }
+        if (st && status != PM_ERR_CUDA)
+            for (int k = 0; k < S.nprob; ++k)
+                for (int d = 0; d < 3; ++d) st[k].q[d] = S.hq[4 * k + d];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st)
+        for (int k = 0; k < S.nprob; ++k) {
+            st[k].iters = iters;
+            st[k].delta = mon[k].delta;
+            st[k].err_est = mon[k].err;
+            st[k].sweep_ms = win_sweeps ? win_ms / (double)win_sweeps : 0.0;
+            st[k].sweeps_timed = win_sweeps;
+            st[k].seconds = now_s() - t0;
+            st[k].status = status;
+        }
+    return status;
+}
+
+template <typename T>
+int iterate_impl(const pm_domain *dom, int dir, double drive, const pm_options *o, int64_t n, T *u, T *p,
+                 cudaStream_t s, Scratch &scr) {
+    Geometry g;
+    int st = build_geometry(dom, s, scr, g);
+    if (st) return st;
+    Solver<T> S(g, *o, s, scr);
+    if ((st = S.init(1))) return st;
+    S.dir[0] = dir;
+    S.force[0] = drive;
+    if ((st = S.load_state(0, u, p))) return st;
+    if (n > 0) {
+        if ((st = S.sweep(kModeU, false))) return st;
+        for (int64_t i = 1; i < n; ++i)
+            if ((st = S.sweep(kModePU, false))) return st;
+        if ((st = S.sweep(kModeP, false))) return st;
+    }
+    PM_CK(cudaMemcpyAsync(u, S.F[0].u[S.F[0].cur], sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
+    PM_CK(cudaMemcpyAsync(p, S.F[0].p[S.F[0].cur], sizeof(T) * g.N, cudaMemcpyDeviceToDevice, s));
+    return PM_OK;
+}
+
+// Solve a batch of drive directions on one geometry.  Fields stay on the device in
+// S.F; the caller extracts what it needs.
+template <typename T>
+int solve_batch(const Geometry &g, const pm_options *o, cudaStream_t s, Scratch &scr, int np, const int *dirs,
+                Solver<T> &S, pm_stats *st, double t0) {
+    int rc = S.init(np);
+    if (rc) return rc;
+    for (int k = 0; k < np; ++k) {
+        S.dir[k] = dirs[k];
+        S.force[k] = 1.0;  // Sec. 4: grad p = 1 per voxel in iteration units
+    }
+    return run_to_convergence<T>(S, st, t0);
+}
+
+int count_fluid(const std::vector<uint8_t> &m) {
+    for (uint8_t v : m)
+        if (!v) return 1;
+    return 0;
+}
+
+template <typename T>
+int tensor_like(const pm_domain *dom, const pm_options *o, int ndirs, const int *dirs_in, double drive,
+                       float *u_out, float *p_out, const float *u0, const float *p0, double kcols[3][3],
+                       pm_stats *st, void *cuda_stream) {
+    const double t0 = now_s();
+    std::vector<uint8_t> hm;
+    int rc = host_mask(dom, hm);
+    if (rc) return rc;
+    if (!count_fluid(hm)) return PM_ERR_NO_FLUID;
+    int per[3] = {dom->bc[0] == PM_BC_PERIODIC, dom->bc[1] == PM_BC_PERIODIC, dom->bc[2] == PM_BC_PERIODIC};
+    int perc[3] = {1, 1, 1};
+    if (o->check_percolation) percolation_host(hm, dom->nx, dom->ny, dom->nz, per, perc);
+    int dirs[3], np = 0, slot[3] = {-1, -1, -1};
+    bool blocked = false;
+    for (int k = 0; k < ndirs; ++k) {
+        if (st) {
+            std::memset(&st[k], 0, sizeof(pm_stats));
+            st[k].percolates = perc[dirs_in[k]];
+        }
+        if (perc[dirs_in[k]]) {
+            slot[k] = np;
+            dirs[np++] = dirs_in[k];
+        } else
+            blocked = true;
+    }
+    for (int k = 0; k < ndirs; ++k)
+        for (int i = 0; i < 3; ++i) kcols[k][i] = 0.0;
+    StreamScope ss(cuda_stream);
+    if (ss.status) return ss.status;
+    int status = PM_OK;
+    pm_stats bst[kMaxBatch];
+    std::memset(bst, 0, sizeof(bst));
+    {
+        Scratch scr(ss.s);
+        Geometry g;
+        if ((rc = build_geometry(dom, ss.s, scr, g))) return rc;
+        if (np > 0) {
+            Solver<T> S(g, *o, ss.s, scr);
+            rc = S.init(np);
+            if (rc) return rc;
+            const double uscale = drive * dom->voxel_size * dom->voxel_size / (dom->viscosity * o->Re);
+            const double pscale = drive * dom->voxel_size;
+            for (int k = 0; k < np; ++k) {
+                S.dir[k] = dirs[k];
+                S.force[k] = 1.0;
+            }
+            if (u0 || p0) {
+                // warm start (single drive only): Darcy-scaled float -> iteration units
+                T *ut = S.F[0].u[0], *pt = S.F[0].p[0];
+                if (u0) scale_copy_kernel<T, float><<<launch_grid(3 * g.N), 256, 0, ss.s>>>(ut, u0, 1.0 / uscale, 3 * g.N);
+                if (p0) scale_copy_kernel<T, float><<<launch_grid(g.N), 256, 0, ss.s>>>(pt, p0, 1.0 / pscale, g.N);
+                sanitize_kernel<T><<<launch_grid(g.N), 256, 0, ss.s>>>(g.flags, g.N, ut, pt);
+                if (cudaGetLastError() != cudaSuccess) return PM_ERR_CUDA;
+            }
+            status = run_to_convergence<T>(S, bst, t0);
+            if (status == PM_OK || status == PM_ERR_NOT_CONVERGED) {
+                if (u_out)
+                    scale_copy_kernel<float, T><<<launch_grid(3 * g.N), 256, 0, ss.s>>>(u_out, S.F[0].u[S.F[0].cur],
+                                                                                       uscale, 3 * g.N);
+                if (p_out)
+                    scale_copy_kernel<float, T><<<launch_grid(g.N), 256, 0, ss.s>>>(p_out, S.F[0].p[S.F[0].cur],
+                                                                                   pscale, g.N);
+                if (cudaGetLastError() != cudaSuccess) status = PM_ERR_CUDA;
+            }
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(ss.s);
+    if (e != cudaSuccess && status == PM_OK) status = map_cuda(e);
+    for (int k = 0; k < ndirs; ++k) {
+        if (slot[k] < 0) continue;
+        const pm_stats &b = bst[slot[k]];
+        // Appendix C: k_ij = mu q_i^(j) / h_j; iteration units mu = 1/Re, h = 1 -> q / Re
+        for (int i = 0; i < 3; ++i) kcols[k][i] = b.q[i] / o->Re * dom->voxel_size * dom->voxel_size;
+        if (st) {
+            int perc_k = st[k].percolates;
+            st[k] = b;
+            st[k].percolates = perc_k;
+        }
+    }
+    if (status == PM_OK && blocked) status = PM_ERR_NOT_PERCOLATING;
+    return status;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void pm_default_options(pm_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->check_every = 200;
+    o->max_iter = 2000000;
+    o->precision = PM_FP32_RED64;
+    o->dt_safety = 0.9;
+    o->Re = 0.01;
+    o->c2 = 1.5e6;
+    o->use_graph = 1;
+    o->check_percolation = 1;
+    o->dc_switch_tol = 1e-5;
+    o->dc_max_rounds = 8;
+    o->kernel = 0;
+}
+
+const char *pm_strerror(int s) {
+    switch (s) {
+    case PM_OK: return "ok";
+    case PM_ERR_INVALID_ARG: return "invalid argument";
+    case PM_ERR_NO_FLUID: return "the mask has no pore voxel";
+    case PM_ERR_NOT_PERCOLATING: return "no fluid path wraps the domain along a drive axis";
+    case PM_ERR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
+    case PM_ERR_DIVERGED: return "non-finite values in the iteration";
+    case PM_ERR_OOM: return "device memory allocation failed";
+    case PM_ERR_CUDA: return "CUDA runtime error";
+    case PM_ERR_TIMEOUT: return "bounded device wait ran out";
+    case PM_ERR_UNSUPPORTED: return "option combination not supported";
+    default: return "unknown status";
+    }
+}
+
+int pm_version(void) { return kVersion; }
+
+double pm_time_step(const pm_options *o) { return o ? time_step(o) : 0.0; }
+
+int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_options *o, int64_t n, void *u, void *p,
+               void *cuda_stream) {
+    int st = validate_domain(dom);
+    if (st) return st;
+    if ((st = validate_options(o))) return st;
+    if (dir < 0 || dir > 2 || !u || !p || n < 0) return PM_ERR_INVALID_ARG;
+    if (o->precision == PM_FP32_DC64) return PM_ERR_INVALID_ARG;
+    StreamScope ss(cuda_stream);
+    if (ss.status) return ss.status;
+    {
+        Scratch scr(ss.s);
+        if (o->precision == PM_FP64)
+            st = iterate_impl<double>(dom, dir, drive, o, n, (double *)u, (double *)p, ss.s, scr);
+        else
+            st = iterate_impl<float>(dom, dir, drive, o, n, (float *)u, (float *)p, ss.s, scr);
+    }
+    cudaError_t e = cudaStreamSynchronize(ss.s);
+    if (!st && e != cudaSuccess) st = map_cuda(e);
+    return st;
+}
+
+int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_options *o, float *u, float *p,
+                       const float *u0, const float *p0, double *k_col, pm_stats *st, void *cuda_stream) {
+    int rc = validate_domain(dom);
+    if (rc) return rc;
+    if ((rc = validate_options(o))) return rc;
+    if (dir < 0 || dir > 2 || !(drive > 0)) return PM_ERR_INVALID_ARG;
+    if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
+    double kc[3][3];
+    pm_stats local;
+    int dirs[1] = {dir};
+    if (o->precision == PM_FP64)
+        rc = tensor_like<double>(dom, o, 1, dirs, drive, u, p, u0, p0, kc, st ? st : &local, cuda_stream);
+    else
+        rc = tensor_like<float>(dom, o, 1, dirs, drive, u, p, u0, p0, kc, st ? st : &local, cuda_stream);
+    if (k_col)
+        for (int i = 0; i < 3; ++i) k_col[i] = kc[0][i];
+    return rc;
+}
+
+int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_options *o, double k_out[9],
+                           double k_raw[9], pm_stats st[3], void *cuda_stream) {
+    int rc = validate_domain(dom);
+    if (rc) return rc;
+    if ((rc = validate_options(o))) return rc;
+    if (!k_out || !(drive > 0)) return PM_ERR_INVALID_ARG;
+    if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
+    double kc[3][3];
+    int dirs[3] = {0, 1, 2};
+    if (o->precision == PM_FP64)
+        rc = tensor_like<double>(dom, o, 3, dirs, drive, nullptr, nullptr, nullptr, nullptr, kc, st, cuda_stream);
+    else
+        rc = tensor_like<float>(dom, o, 3, dirs, drive, nullptr, nullptr, nullptr, nullptr, kc, st, cuda_stream);
+    // kc[j][i] = k_ij (column j from drive j); Sec. 6.4 / Appendix C: average off-diagonals
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (k_raw) k_raw[3 * i + j] = kc[j][i];
+            k_out[3 * i + j] = 0.5 * (kc[j][i] + kc[i][j]);
+        }
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Shared device definitions of the GB300 permeability solver.
+//
+// Grid and unknowns (Sec. 4, "Grid"): MAC grid, p at cell centres, u_d on the +d face of
+// each cell, fields stored as separate arrays [nz][ny][nx] (x fastest).  A face node
+// u_d(c) is fluid iff cells c and c+e_d are both pore; the other nodes are
+// no-penetration faces and hold exactly 0 in every buffer, so a stencil may read them
+// without testing the mask.
+//
+// Neighbourhood flags (Algorithm 1, "Evaluate neighborhood"), one byte per cell:
+//   bit 0  cell c is pore
+//   bit 1  node u_x(c) is fluid, bit 2 node u_y(c), bit 3 node u_z(c)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pmgb {
+
+constexpr int kFlagCell = 1;
+__host__ __device__ constexpr int node_bit(int d) { return 2 << d; }
+
+// Sweep variants.  The fused sweep works on the staggered state (u^n, p^{n-1}): it first
+// forms p^n = p^{n-1} - dt c^2 (D u^n - r_p) on the cells it needs, then
+// u^{n+1} = u^n + dt R_u(u^n, p^n).  This is exactly the paper's order (velocity update,
+// then pressure update with the new velocity) regrouped so that one pass reads each
+// field once: the pressure of iteration n is finished in the pass that also does the
+// velocity of iteration n+1.
+enum SweepMode : int {
+    kModeU = 1,   // u^{1} from (u^0, p^0); p copied (first iteration)
+    kModePU = 2,  // p^n from (u^n, p^{n-1}), then u^{n+1}
+    kModeP = 3    // p^n only (last half-step, brings p level with u)
+};
+
+template <typename T>
+struct SweepProblem {
+    const T *uin;    // 3N
+    const T *pin;    // N
+    T *uout;         // 3N
+    T *pout;         // N
+    const T *src;    // 4N source (r_u x3, r_p) or nullptr
+    T f[3];          // body force per face direction (the drive)
+    double *partials;  // [nblocks][4] block sums (q_x, q_y, q_z, |div|^2) or nullptr
+};
+
+constexpr int kMaxBatch = 4;
+
+template <typename T>
+struct SweepBatch {
+    int nx, ny, nz;
+    int per[3];            // 1 = periodic axis, 0 = wall (outside counts as solid)
+    long long N;
+    const uint8_t *flags;  // N
+    const T *alpha;        // N per-cell drag or nullptr
+    T inv_re, dt, dtc2;
+    int nprob;
+    SweepProblem<T> prob[kMaxBatch];
+};
+
+// Neighbour coordinate v (= x + m, |m| <= 2) on an axis of n cells: periodic wrap, or -1
+// outside a wall axis.
+__device__ __forceinline__ int nb_coord(int v, int n, int periodic) {
+    if (v < 0) {
+        if (!periodic) return -1;
+        do { v += n; } while (v < 0);
+    } else if (v >= n) {
+        if (!periodic) return -1;
+        do { v -= n; } while (v >= n);
+    }
+    return v;
+}
+
+}  // namespace pmgb

@@ -1,0 +1,219 @@
+// Device kernels of the GB300 permeability solver: neighbourhood evaluation, the fused
+// pseudo-time sweep, FP64 reductions and small field utilities.
+#pragma once
+
+#include "pm_common.cuh"
+
+namespace pmgb {
+
+// ------------------------------------------------------------------ neighbourhood
+// Algorithm 1 "Evaluate neighborhood": per cell the pore flag and the fluid flags of its
+// three +d face nodes (Sec. 4: a face between two pore cells carries flow; every face
+// touching solid is a no-slip / no-penetration face).
+__global__ void classify_kernel(const uint8_t *__restrict__ mask, int nx, int ny, int nz, int px,
+                                int py, int pz, uint8_t *__restrict__ flags) {
+    long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(c % nx);
+        long long r = c / nx;
+        int y = (int)(r % ny);
+        int z = (int)(r / ny);
+        uint8_t f = 0;
+        if (!mask[c]) {
+            f |= kFlagCell;
+            int xp = nb_coord(x + 1, nx, px), yp = nb_coord(y + 1, ny, py), zp = nb_coord(z + 1, nz, pz);
+            if (xp >= 0 && !mask[xp + (long long)nx * (y + (long long)ny * z)]) f |= node_bit(0);
+            if (yp >= 0 && !mask[x + (long long)nx * (yp + (long long)ny * z)]) f |= node_bit(1);
+            if (zp >= 0 && !mask[x + (long long)nx * (y + (long long)ny * zp)]) f |= node_bit(2);
+        }
+        flags[c] = f;
+    }
+}
+
+// Zero the values on non-fluid faces and solid cells (the invariant every sweep relies
+// on), used on caller-provided starting fields.
+template <typename T>
+__global__ void sanitize_kernel(const uint8_t *__restrict__ flags, long long N, T *u, T *p) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        uint8_t f = flags[c];
+        for (int d = 0; d < 3; ++d)
+            if (!(f & node_bit(d))) u[d * N + c] = T(0);
+        if (!(f & kFlagCell)) p[c] = T(0);
+    }
+}
+
+// ------------------------------------------------------------------ wall stencil
+// Sec. 4 / Appendix B: second derivative of a face velocity along an axis perpendicular
+// to its direction, from the node itself (u0) and the nodes at -2, -1, +1, +2 with their
+// fluid flags.  A missing neighbour at +-1 is a no-slip wall half a spacing away.
+//   case 1  walls on both sides         -8 u0
+//   case 2  wall at -1/2, no node at +2  (8 u(+1) - 16 u0) / 3
+//   case 3  mirror of case 2             (8 u(-1) - 16 u0) / 3
+//   case 4  wall at -1/2, node at +2     2 u(+1) - 5 u0 - u(+2) / 5
+//   case 5  mirror of case 4             2 u(-1) - 5 u0 - u(-2) / 5
+//   case 6  both neighbours fluid        u(-1) - 2 u0 + u(+1)
+// Non-fluid node values are exactly 0, so the selects only choose coefficients.
+template <typename T>
+__device__ __forceinline__ T perp_d2(T u0, T um2, T um1, T up1, T up2, bool Fm2, bool Fm1, bool Fp1,
+                                     bool Fp2) {
+    const T c83 = T(8) / T(3), c163 = T(16) / T(3), c15 = T(1) / T(5);
+    if (Fm1 && Fp1) return um1 - T(2) * u0 + up1;
+    if (!Fm1 && !Fp1) return T(-8) * u0;
+    if (Fp1) return Fp2 ? (T(2) * up1 - T(5) * u0 - c15 * up2) : (c83 * up1 - c163 * u0);
+    return Fm2 ? (T(2) * um1 - T(5) * u0 - c15 * um2) : (c83 * um1 - c163 * u0);
+}
+
+// ------------------------------------------------------------------ simple fused sweep
+// Reference implementation: one thread per cell, every operand loaded from global memory
+// (L1/L2 serve the neighbour reuse).  It defines the arithmetic the tiled kernel must
+// reproduce and serves small domains.
+template <typename T, int MODE, bool REDUCE, bool SRC>
+__global__ void __launch_bounds__(256) sweep_simple_kernel(const SweepBatch<T> B) {
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const long long N = B.N;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z % nz;
+    const int pi = blockIdx.z / nz;
+    const SweepProblem<T> &P = B.prob[pi];
+    const bool active = (x < nx) && (y < ny);
+    const uint8_t *__restrict__ fl = B.flags;
+
+    auto lin = [&](int xx, int yy, int zz) -> long long {
+        return (long long)xx + (long long)nx * ((long long)yy + (long long)ny * zz);
+    };
+    // coordinates of neighbours, -1 outside a wall axis
+    auto cx = [&](int m) { return nb_coord(x + m, nx, B.per[0]); };
+    auto cy = [&](int m) { return nb_coord(y + m, ny, B.per[1]); };
+    auto cz = [&](int m) { return nb_coord(z + m, nz, B.per[2]); };
+    auto U = [&](int d, int xx, int yy, int zz) -> T {
+        if (xx < 0 || yy < 0 || zz < 0) return T(0);
+        return P.uin[d * N + lin(xx, yy, zz)];
+    };
+    auto F = [&](int d, int xx, int yy, int zz) -> bool {
+        if (xx < 0 || yy < 0 || zz < 0) return false;
+        return (fl[lin(xx, yy, zz)] & node_bit(d)) != 0;
+    };
+    // p^n at a cell (MODE kModeU: p^n is the input)
+    T div_own = T(0);
+    auto pn = [&](int xx, int yy, int zz, bool own) -> T {
+        long long c = lin(xx, yy, zz);
+        if (!(fl[c] & kFlagCell)) return T(0);
+        T p0 = P.pin[c];
+        if (MODE == kModeU) return p0;
+        int xm = nb_coord(xx - 1, nx, B.per[0]), ym = nb_coord(yy - 1, ny, B.per[1]),
+            zm = nb_coord(zz - 1, nz, B.per[2]);
+        T dv = (P.uin[c] - U(0, xm, yy, zz)) + (P.uin[N + c] - U(1, xx, ym, zz)) +
+               (P.uin[2 * N + c] - U(2, xx, yy, zm));
+        if (own) div_own = dv;
+        T rp = SRC ? P.src[3 * N + c] : T(0);
+        return p0 - B.dtc2 * (dv - rp);
+    };
+
+    T unew[3] = {T(0), T(0), T(0)};
+    if (active) {
+        const long long c = lin(x, y, z);
+        const uint8_t f0 = fl[c];
+        const T p_c = pn(x, y, z, true);
+        P.pout[c] = p_c;
+        if (MODE == kModeP)
+            for (int d = 0; d < 3; ++d) P.uout[d * N + c] = P.uin[d * N + c];
+        if (MODE != kModeP) {
+            const int xm1 = cx(-1), xp1 = cx(1), xm2 = cx(-2), xp2 = cx(2);
+            const int ym1 = cy(-1), yp1 = cy(1), ym2 = cy(-2), yp2 = cy(2);
+            const int zm1 = cz(-1), zp1 = cz(1), zm2 = cz(-2), zp2 = cz(2);
+            for (int d = 0; d < 3; ++d) {
+                T un = T(0);
+                if (f0 & node_bit(d)) {
+                    const T u0 = P.uin[d * N + c];
+                    T lap;
+                    // along the flow direction: 3-point, non-fluid neighbours are 0
+                    if (d == 0) lap = U(0, xp1, y, z) - T(2) * u0 + U(0, xm1, y, z);
+                    else if (d == 1) lap = U(1, x, yp1, z) - T(2) * u0 + U(1, x, ym1, z);
+                    else lap = U(2, x, y, zp1) - T(2) * u0 + U(2, x, y, zm1);
+                    if (d != 0)
+                        lap += perp_d2(u0, U(d, xm2, y, z), U(d, xm1, y, z), U(d, xp1, y, z), U(d, xp2, y, z),
+                                       F(d, xm2, y, z), F(d, xm1, y, z), F(d, xp1, y, z), F(d, xp2, y, z));
+                    if (d != 1)
+                        lap += perp_d2(u0, U(d, x, ym2, z), U(d, x, ym1, z), U(d, x, yp1, z), U(d, x, yp2, z),
+                                       F(d, x, ym2, z), F(d, x, ym1, z), F(d, x, yp1, z), F(d, x, yp2, z));
+                    if (d != 2)
+                        lap += perp_d2(u0, U(d, x, y, zm2), U(d, x, y, zm1), U(d, x, y, zp1), U(d, x, y, zp2),
+                                       F(d, x, y, zm2), F(d, x, y, zm1), F(d, x, y, zp1), F(d, x, y, zp2));
+                    // the +d cell exists and is pore because the node is fluid
+                    int ex = d == 0 ? xp1 : x, ey = d == 1 ? yp1 : y, ez = d == 2 ? zp1 : z;
+                    if (B.alpha) lap -= T(0.5) * (B.alpha[c] + B.alpha[lin(ex, ey, ez)]) * u0;
+                    const T grad = pn(ex, ey, ez, false) - p_c;
+                    T R = B.inv_re * lap - grad + P.f[d];
+                    if (SRC) R += P.src[d * N + c];
+                    un = u0 + B.dt * R;
+                }
+                unew[d] = un;
+                P.uout[d * N + c] = un;
+            }
+        }
+    }
+    if (REDUCE) {
+        // FP64 block reduction: warp shuffles, then one partial per warp in shared memory
+        double v[4];
+        if (MODE == kModeP) {
+            if (active) {
+                long long c = lin(x, y, z);
+                v[0] = (double)P.uin[c]; v[1] = (double)P.uin[N + c]; v[2] = (double)P.uin[2 * N + c];
+            } else v[0] = v[1] = v[2] = 0.0;
+        } else {
+            v[0] = (double)unew[0]; v[1] = (double)unew[1]; v[2] = (double)unew[2];
+        }
+        v[3] = active ? (double)div_own * (double)div_own : 0.0;
+        for (int k = 0; k < 4; ++k)
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        __shared__ double sred[8][4];
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        const int warp = tid >> 5, lane = tid & 31;
+        if (lane == 0)
+            for (int k = 0; k < 4; ++k) sred[warp][k] = v[k];
+        __syncthreads();
+        if (tid < 4) {
+            double s = 0.0;
+            const int nw = (blockDim.x * blockDim.y) >> 5;
+            for (int w = 0; w < nw; ++w) s += sred[w][tid];
+            const long long blk = (long long)blockIdx.x + (long long)gridDim.x *
+                                  ((long long)blockIdx.y + (long long)gridDim.y * (long long)z);
+            P.partials[blk * 4 + tid] = s;
+        }
+    }
+}
+
+// Sums the block partials of each problem in a fixed order (deterministic) and scales
+// by 1/N: out[prob][0..2] = q_d, out[prob][3] = |D u|^2.
+__global__ void reduce_partials_kernel(const double *partials, long long nblk, long long N,
+                                       double *out) {
+    const double *P = partials + (size_t)blockIdx.x * nblk * 4;
+    __shared__ double s[256][4];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long b = threadIdx.x; b < nblk; b += blockDim.x)
+        for (int k = 0; k < 4; ++k) a[k] += P[b * 4 + k];
+    for (int k = 0; k < 4; ++k) s[threadIdx.x][k] = a[k];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int k = 0; k < 4; ++k) s[threadIdx.x][k] += s[threadIdx.x + st][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) out[blockIdx.x * 4 + k] = s[0][k] / (double)N;
+        out[blockIdx.x * 4 + 3] = s[0][3];
+    }
+}
+
+// y = a * x (type conversion allowed), n elements.
+template <typename TO, typename TI>
+__global__ void scale_copy_kernel(TO *__restrict__ y, const TI *__restrict__ x, double a, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = (TO)(a * (double)x[i]);
+}
+
+}  // namespace pmgb

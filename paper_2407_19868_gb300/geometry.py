@@ -109,13 +109,16 @@ def _min_scaled_distance(shape, centres, radii, s_max: float) -> np.ndarray:
 
 def rsa_sphere_pack(shape, median: float, sigma: float, r_min: float, r_max: float,
                     target_porosity: float, seed: int, max_rejections: int = 20000,
-                    n_radii: int = 20000, s_max: float = 1.6):
+                    attempts_per_sphere: int = 500, fill: float = 0.45, s_max: float = 1.6):
     """Consolidated random sphere pack.
 
-    1. Radii r = median * exp(sigma * N(0, 1)) clipped to [r_min, r_max]; sorted,
-       largest first.
+    1. Radii r = median * exp(sigma * N(0, 1)) clipped to [r_min, r_max], drawn until
+       their total sphere volume reaches ``fill`` x the box volume; sorted, largest
+       first.
     2. Random sequential addition of non-overlapping spheres (periodic minimum
-       image) until ``max_rejections`` consecutive rejected trials.
+       image): each radius gets up to ``attempts_per_sphere`` random centres and is
+       skipped if none fits; addition stops after ``max_rejections`` consecutive
+       rejected trials (jamming) or when the radii run out.
     3. Non-overlapping addition jams well above porosity 0.38, so all radii are
        then dilated by one common factor s (overlaps allowed) chosen so that the
        porosity equals the target (to one voxel).
@@ -125,28 +128,40 @@ def rsa_sphere_pack(shape, median: float, sigma: float, r_min: float, r_max: flo
     nz, ny, nx = shape
     box = np.array([nx, ny, nz], dtype=np.float64)
     g = rng(seed)
-    radii = np.clip(median * np.exp(sigma * g.standard_normal(n_radii)), r_min, r_max)
-    radii = np.sort(radii)[::-1]
-    centres = np.zeros((0, 3))
-    acc_r = np.zeros(0)
+    radii = []
+    vol = 0.0
+    while vol < fill * float(nx * ny * nz):
+        r = float(np.clip(median * np.exp(sigma * g.standard_normal()), r_min, r_max))
+        radii.append(r)
+        vol += 4.0 / 3.0 * np.pi * r**3
+    radii = np.sort(np.array(radii))[::-1]
+    n_radii = len(radii)
+    centres = np.zeros((n_radii, 3))
+    acc_r = np.zeros(n_radii)
+    n_acc = 0
     rejections = 0
-    k = 0
-    while k < len(radii) and rejections < max_rejections:
-        r = radii[k]
-        c = g.random(3) * box
-        if len(acc_r):
-            d = centres - c
-            d -= box * np.round(d / box)
-            ok = np.all(np.einsum("ij,ij->i", d, d) >= (acc_r + r) ** 2)
-        else:
-            ok = True
-        if ok:
-            centres = np.vstack([centres, c])
-            acc_r = np.append(acc_r, r)
-            rejections = 0
-            k += 1
-        else:
+    for r in radii:
+        if rejections >= max_rejections:
+            break
+        for _ in range(attempts_per_sphere):
+            c = g.random(3) * box
+            if n_acc:
+                d = centres[:n_acc] - c
+                d -= box * np.round(d / box)
+                ok = bool(np.all(np.einsum("ij,ij->i", d, d) >= (acc_r[:n_acc] + r) ** 2))
+            else:
+                ok = True
+            if ok:
+                centres[n_acc] = c
+                acc_r[n_acc] = r
+                n_acc += 1
+                rejections = 0
+                break
             rejections += 1
+            if rejections >= max_rejections:
+                break
+    centres = centres[:n_acc]
+    acc_r = acc_r[:n_acc]
     m = _min_scaled_distance(shape, centres, acc_r, s_max)
     n_fluid = int(round(target_porosity * m.size))
     flat = np.sort(m, axis=None)

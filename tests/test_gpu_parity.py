@@ -1,0 +1,155 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle.
+
+Trajectories are compared element by element after 1, 2 and 10 iterations of
+Algorithm 1 (same inputs, same order of updates); converged permeabilities are
+compared per component.
+
+Tolerances (derived from the arithmetic):
+* FP64 fields: the GPU contracts a*b+c into FMAs and sums in another order, so each
+  value differs by a few ulp per iteration -> 1e-11 relative to the field's max.
+* FP32 fields: one FP32 rounding per operation, ~30 operations per update, errors do
+  not grow within a few iterations -> 2e-5 relative to the field's max.
+* Converged k: the BASELINE target, 1e-5 relative per component, with off-diagonal
+  components compared against 1e-5 x max |k_ii| (they are differences of near-equal
+  fluxes and carry the diagonal's absolute error).
+"""
+import numpy as np
+import pytest
+
+from paper_2407_19868_gb300 import geometry as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2407_19868_gb300 import api as A
+    A.load()
+    return A
+
+
+def _gpu_iterate(api, mask, n, drive_dir, precision, bc=(0, 0, 0), U0=None, p0=None, **kw):
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    nz, ny, nx = mask.shape
+    u = torch.zeros((3, nz, ny, nx), dtype=dt, device="cuda")
+    p = torch.zeros((nz, ny, nx), dtype=dt, device="cuda")
+    if U0 is not None:
+        u.copy_(torch.from_numpy(U0))
+        p.copy_(torch.from_numpy(p0))
+    api.iterate(torch.from_numpy(mask).cuda(), u, p, n, drive_dir=drive_dir, bc=bc, precision=precision, **kw)
+    torch.cuda.synchronize()
+    return u.double().cpu().numpy(), p.double().cpu().numpy()
+
+
+def _oracle_iterate(oracle_mod, mask, n, drive_dir, bc=(0, 0, 0), U0=None, p0=None, dt=None):
+    dom = oracle_mod.Domain(mask, bc=bc)
+    U, p = dom.zeros()
+    if U0 is not None:
+        U[...] = U0
+        p[...] = p0
+    dom.iterate(U, p, n, drive_dir=drive_dir, dt=dt)
+    return U, p
+
+
+CASES = [
+    ("odd_random", lambda: G.random_blocks((5, 7, 9), 0.3, seed=1), (0, 0, 0)),
+    ("spheres_ragged", lambda: G.overlapping_spheres((11, 13, 37), 2.5, 0.6, seed=2), (0, 0, 0)),
+    ("walls_y", lambda: G.overlapping_spheres((8, 10, 12), 2.0, 0.7, seed=3), (0, 1, 0)),
+    ("walls_xz", lambda: G.random_blocks((6, 9, 33), 0.25, seed=4), (1, 0, 1)),
+    ("thin_n1", lambda: G.random_blocks((1, 12, 40), 0.3, seed=5), (0, 0, 0)),
+    ("thin_n2", lambda: G.random_blocks((2, 3, 17), 0.2, seed=6), (0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("name,make,bc", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", [1, 0], ids=["simple", "default"])
+def test_trajectory_matches_oracle(api, oracle_mod, name, make, bc, precision, kernel):
+    mask = make()
+    dt = api.time_step()
+    for n in (1, 2, 10):
+        for drive_dir in (0, 2):
+            Ug, pg = _gpu_iterate(api, mask, n, drive_dir, precision, bc=bc, kernel=kernel)
+            Uo, po = _oracle_iterate(oracle_mod, mask, n, drive_dir, bc=bc, dt=dt)
+            tol = 1e-11 if precision == "fp64" else 2e-5
+            su, sp = max(np.abs(Uo).max(), 1e-300), max(np.abs(po).max(), 1e-300)
+            np.testing.assert_allclose(Ug, Uo, rtol=0, atol=tol * su, err_msg=f"u n={n} dir={drive_dir}")
+            np.testing.assert_allclose(pg, po, rtol=0, atol=tol * sp, err_msg=f"p n={n} dir={drive_dir}")
+            nf, _ = oracle_mod.Domain(mask, bc=bc).tables()
+            assert np.all(Ug[nf == 0] == 0.0)
+
+
+def test_warm_start_trajectory(api, oracle_mod):
+    mask = G.overlapping_spheres((10, 12, 14), 2.5, 0.65, seed=8)
+    rng = G.rng(9)
+    U0 = rng.standard_normal((3,) + mask.shape) * 1e-3
+    p0 = rng.standard_normal(mask.shape)
+    Ug, pg = _gpu_iterate(api, mask, 3, 1, "fp64", U0=U0, p0=p0)
+    Uo, po = _oracle_iterate(oracle_mod, mask, 3, 1, U0=np.where(oracle_mod.Domain(mask).tables()[0] == 1, U0, 0.0),
+                             p0=np.where(mask == 0, p0, 0.0), dt=api.time_step())
+    np.testing.assert_allclose(Ug, Uo, rtol=0, atol=1e-11 * np.abs(Uo).max())
+    np.testing.assert_allclose(pg, po, rtol=0, atol=1e-11 * np.abs(po).max())
+
+
+@pytest.fixture(scope="module")
+def config1():
+    # 32^3 periodic, overlapping spheres r = 4 to porosity 0.70, seed 1
+    return G.overlapping_spheres((32, 32, 32), 4.0, 0.70, seed=1)
+
+
+@pytest.fixture(scope="module")
+def config1_oracle(oracle_mod, config1):
+    r = oracle_mod.Domain(config1).solve(0, tol=1e-11, check_every=100)
+    assert r["iters"] > 0
+    return r["q"] / oracle_mod.RE_PAPER
+
+
+@pytest.mark.parametrize("precision,tol,rel", [("fp64", 1e-11, 1e-9), ("fp32", 1e-9, 1e-5)])
+def test_config1_kxx_converged(api, config1, config1_oracle, precision, tol, rel):
+    r = api.solve_direction(config1, 0, tol=tol, precision=precision, check_every=100)
+    assert r["status"] == api.PM_OK
+    k = r["k_col"]
+    ko = config1_oracle
+    assert k[0] == pytest.approx(ko[0], rel=rel)
+    np.testing.assert_allclose(k[1:], ko[1:], rtol=0, atol=rel * abs(ko[0]))
+    # returned fields: Darcy-scaled (drive = dx = mu = 1 -> mean u_x = k_xx)
+    u = r["u"].double()
+    assert float(u[0].mean()) == pytest.approx(k[0], rel=1e-6)
+
+
+def test_full_tensor_batched(api, oracle_mod):
+    mask = G.overlapping_spheres((20, 24, 28), 3.0, 0.6, seed=12)
+    k_sym_o, k_raw_o, _ = oracle_mod.ktensor(mask, tol=1e-11)
+    scale = np.abs(np.diag(k_raw_o)).max()
+    for prec, tol, rel in (("fp64", 1e-11, 1e-9), ("fp32", 1e-9, 1e-5)):
+        r = api.permeability_tensor(mask, tol=tol, precision=prec)
+        assert r["status"] == api.PM_OK
+        np.testing.assert_allclose(r["k_raw"], k_raw_o, rtol=0, atol=rel * scale)
+        np.testing.assert_allclose(r["k"], k_sym_o, rtol=0, atol=rel * scale)
+        np.testing.assert_allclose(np.diag(r["k"]), np.diag(k_sym_o), rtol=rel)
+
+
+def test_non_percolating_axis(api):
+    m = G.slit(8, 3, 6, nz=4)  # walls normal to y: no flow along y
+    r = api.permeability_tensor(m, tol=1e-10, precision="fp64")
+    assert r["status"] == api.PM_ERR_NOT_PERCOLATING
+    assert not r["stats"][1]["percolates"]
+    assert np.all(r["k"][1, :] == 0) and np.all(r["k"][:, 1] == 0)
+    assert r["k"][0, 0] == pytest.approx(3 * (2 * 9 + 1) / (24 * 6), rel=1e-9)
+
+
+def test_slit_exact_on_gpu(api):
+    for h, P in ((1, 3), (2, 4), (5, 8)):
+        m = G.slit(32, h, P, nz=3)
+        r = api.solve_direction(m, 0, tol=1e-13, precision="fp64", check_every=100)
+        assert r["k_col"][0] == pytest.approx(h * (2 * h * h + 1) / (24 * P), rel=1e-10)
+
+
+def test_no_fluid_is_an_error(api):
+    with pytest.raises(api.PMError) as e:
+        api.solve_direction(np.ones((4, 4, 4), dtype=np.uint8), 0)
+    assert e.value.status == api.PM_ERR_NO_FLUID
