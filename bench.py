@@ -276,7 +276,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "dc64", "fp64"])
     ap.add_argument("--check-every", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--cpu-iters", type=int, default=30)
+    ap.add_argument("--cpu-iters", type=int, default=300)
     ap.add_argument("--ref-iters", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -113,8 +113,8 @@ struct Geometry {
     int nx = 0, ny = 0, nz = 0;
     int per[3] = {1, 1, 1};
     long long N = 0;
-    uint8_t *flags = nullptr;  // device
-    long long n_fluid_cells = 0;
+    uint8_t *flags = nullptr;   // device, one byte per cell (simple kernel)
+    uint32_t *code = nullptr;   // device, one stencil code word per cell (tiled kernel)
 };
 
 int validate_domain(const pm_domain *dom) {
@@ -163,6 +163,9 @@ int build_geometry(const pm_domain *dom, cudaStream_t s, Scratch &scr, Geometry 
     }
     classify_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
                                                      g.flags);
+    PM_CK(cudaGetLastError());
+    if ((st = scr.alloc(&g.code, (size_t)g.N))) return st;
+    code_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.code);
     PM_CK(cudaGetLastError());
     return PM_OK;
 }
@@ -267,6 +270,8 @@ struct Solver {
         inv_re = (T)(1.0 / o.Re);
         dim3 gr = grid();
         nblk = (long long)gr.x * gr.y * g.nz;
+        const long long nblk_t = tiled_num_blocks<T>(g.nx, g.ny, g.nz);
+        const long long nblk_max = nblk > nblk_t ? nblk : nblk_t;
         int st;
         for (int k = 0; k < nprob; ++k) {
             for (int b = 0; b < 2; ++b) {
@@ -277,7 +282,7 @@ struct Solver {
             }
             F[k].cur = 0;
         }
-        if ((st = scr.alloc(&partials, (size_t)(nprob * nblk * 4)))) return st;
+        if ((st = scr.alloc(&partials, (size_t)(nprob * nblk_max * 4)))) return st;
         if ((st = scr.alloc(&dq, (size_t)(nprob * 4)))) return st;
         PM_CK(cudaMallocHost(&hq, sizeof(double) * nprob * 4));
         return PM_OK;
@@ -333,7 +338,7 @@ struct Solver {
         for (int k = 0; k < nprob; ++k) has_src |= src[k] != nullptr;
         const bool tiled = o.kernel == 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
         if (tiled) {
-            int st = launch_tiled<T>(B, mode, reduce, has_src, s);
+            int st = launch_tiled<T>(B, g.code, mode, reduce, has_src, s);
             if (st) return st;
         } else if (mode == kModeU) {
             reduce ? launch_simple<kModeU, true>(B, has_src) : launch_simple<kModeU, false>(B, has_src);

@@ -1,0 +1,60 @@
+"""Writes the oracle's converged permeabilities for the benchmark geometries.
+
+Calls only ``oracle/`` and the seeded input generators; nothing here touches the
+CUDA library.  Each entry records the mask's SHA-256 so a test can check it is
+comparing the same geometry.
+
+    python tests/golden/make_reference.py config1 config2
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+from paper_2407_19868_gb300 import geometry as G  # noqa: E402
+
+OUT = os.path.join(HERE, "reference_k.json")
+
+
+def config1():
+    # 32^3 periodic, overlapping spheres r = 4 to porosity 0.70, seed 1; drive x
+    return G.overlapping_spheres((32, 32, 32), 4.0, 0.70, seed=1), (0,), 1e-11
+
+
+def config2():
+    # 256^3 periodic RSA pack, lognormal radii (median 10, sigma 0.3), porosity 0.38, seed 2
+    m, _ = G.rsa_sphere_pack((256, 256, 256), 10.0, 0.3, 4.0, 25.0, 0.38, seed=2)
+    return m, (0, 1, 2), 1e-8
+
+
+CONFIGS = {"config1": config1, "config2": config2}
+
+
+def main(names):
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in names:
+        mask, dirs, tol = CONFIGS[name]()
+        t = time.time()
+        dom = oracle.Domain(mask)
+        cols = {}
+        for j in dirs:
+            r = dom.solve(j, tol=tol, check_every=100)
+            cols[str(j)] = {"q": r["q"].tolist(), "k_col": (r["q"] / oracle.RE_PAPER).tolist(),
+                            "iters": r["iters"], "delta": r["delta"], "err_est": r["err_est"]}
+            print(name, j, cols[str(j)], time.time() - t, flush=True)
+        data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+        data[name] = {"sha256": G.mask_sha256(mask), "shape": list(mask.shape),
+                      "porosity": G.porosity(mask), "tol": tol, "dirs": list(dirs), "columns": cols,
+                      "oracle_threads": oracle.num_threads(), "seconds": time.time() - t,
+                      "dt": oracle.default_dt(), "Re": oracle.RE_PAPER, "c2": oracle.C2_PAPER}
+        with open(OUT + ".tmp", "w") as f:
+            json.dump(data, f, indent=1)
+        os.replace(OUT + ".tmp", OUT)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(CONFIGS))
