@@ -22,7 +22,13 @@ namespace pmgb {
 // ------------------------------------------------------------------ stencil codes
 // bit 0          cell is pore
 // bits 1..3      node u_x, u_y, u_z fluid
-// 3-bit fields   Appendix B wall case (1..6, 0 = node not fluid) of node u_d along axis i
+// 3-bit fields   wall case of node u_d along perpendicular axis i (Appendix B), stored as
+//                kind (bits 0-1) and side (bit 2):
+//                  kind 0  case 6, both neighbours fluid      u(-1) + u(+1) - 2 u0
+//                  kind 1  case 1, walls at -1/2 and +1/2     -8 u0
+//                  kind 2  cases 4/5, one wall, node at +-2   2 u(+-1) - 5 u0 - u(+-2) / 5
+//                  kind 3  cases 2/3, one wall, no node at +-2 (8 u(+-1) - 16 u0) / 3
+//                  side 1  the fluid side is + (cases 2, 4); 0 otherwise
 __host__ __device__ constexpr int code_shift(int d, int i) {
     return d == 0 ? (i == 1 ? 4 : 7) : d == 1 ? (i == 0 ? 10 : 13) : (i == 0 ? 16 : 19);
 }
@@ -67,12 +73,12 @@ __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, in
                                                  nx, ny, nz, per);
                     }
                     // Fig. neighborhoodCases / Appendix B
-                    int k;
-                    if (!F[1] && !F[3]) k = 1;
-                    else if (!F[1]) k = F[4] ? 4 : 2;
-                    else if (!F[3]) k = F[0] ? 5 : 3;
-                    else k = 6;
-                    w |= (uint32_t)k << code_shift(d, i);
+                    uint32_t k;
+                    if (!F[1] && !F[3]) k = 1u;                        // case 1
+                    else if (!F[1]) k = (F[4] ? 2u : 3u) | 4u;         // case 4 / 2
+                    else if (!F[3]) k = F[0] ? 2u : 3u;                // case 5 / 3
+                    else k = 0u;                                       // case 6
+                    w |= k << code_shift(d, i);
                 }
             }
         }
@@ -81,17 +87,11 @@ __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, in
 }
 
 // ------------------------------------------------------------------ cp.async helpers
-__device__ __forceinline__ void cp_async_elem(float *s, const float *g) {
+// 16-byte asynchronous global -> shared copies (L2 only: the tile is staged in shared
+// memory, nothing is reused from L1).
+__device__ __forceinline__ void cp_async16(void *s, const void *g) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_elem(double *s, const double *g) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_elem(uint32_t *s, const uint32_t *g) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -100,9 +100,11 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ------------------------------------------------------------------ kernel
-constexpr int kTX = 32, kTY = 8, kHX = kTX + 4, kHY = kTY + 4, kPL = kHX * kHY, kStages = 6;
+// Tile TX x TY cells, thread (tx, ty) owns cell (x0 + tx, y0 + ty).  Shared-memory boxes
+// are BX = TX + 8 wide (x0 - 4 .. x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4 high
+// (y0 - 2 .. y0 + TY + 1); the stencil needs +-2 in x and y.
+constexpr int kTX = 32, kTY = 8, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY, kStages = 6;
 constexpr int kNT = kTX * kTY;
-constexpr int kElemsPerThread = (kPL + kNT - 1) / kNT;
 
 template <typename T>
 struct TiledSmem {
@@ -112,13 +114,24 @@ struct TiledSmem {
     T pin[kStages][kPL];
     uint32_t cd[kStages][kPL];
     T pn[2][kPL];
-    T coef[8][8];  // Appendix B coefficients (offsets -2..+2) per case, rows 0 and 7 zero
 };
 
-__device__ __forceinline__ int ring(int k) { return ((k % kStages) + kStages) % kStages; }
+// Appendix B second derivative across the flow from the 3-bit wall code (kind, side).
+// Non-fluid nodes hold 0, so u(-1) + u(+1) is the one-sided neighbour when a wall is
+// on the other side.
+template <typename T>
+__device__ __forceinline__ T perp_code(uint32_t k3, T um2, T um1, T u0, T up1, T up2) {
+    const uint32_t kind = k3 & 3u;
+    const T v1 = um1 + up1;
+    const T v2 = (k3 & 4u) ? up2 : um2;
+    const T A = kind == 0u ? T(1) : (kind == 2u ? T(2) : T(8) / T(3));
+    const T Bc = kind == 0u ? T(-2) : (kind == 1u ? T(-8) : (kind == 2u ? T(-5) : T(-16) / T(3)));
+    const T C = kind == 2u ? T(-1) / T(5) : T(0);
+    return A * v1 + Bc * u0 + C * v2;
+}
 
 template <typename T, int MODE, bool REDUCE, bool SRC>
-__global__ void __launch_bounds__(kNT, 2)
+__global__ void __launch_bounds__(kNT, 3)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int zchunk, int tiles_x,
                        int tiles_y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,62 +151,63 @@ __global__ void __launch_bounds__(kNT, 2)
     const T *__restrict__ guz = P.uin + 2 * N;
     const T *__restrict__ gp = P.pin;
 
-    if (tid < 64) {
-        const int k = tid >> 3, j = tid & 7;
-        T v = T(0);
-        const T c83 = T(8) / T(3), c163 = T(16) / T(3), c15 = T(1) / T(5);
-        // columns j = 0..4 <-> offsets -2..+2
-        switch (k) {
-        case 1: v = j == 2 ? T(-8) : T(0); break;
-        case 2: v = j == 2 ? -c163 : j == 3 ? c83 : T(0); break;
-        case 3: v = j == 2 ? -c163 : j == 1 ? c83 : T(0); break;
-        case 4: v = j == 2 ? T(-5) : j == 3 ? T(2) : j == 4 ? -c15 : T(0); break;
-        case 5: v = j == 2 ? T(-5) : j == 1 ? T(2) : j == 0 ? -c15 : T(0); break;
-        case 6: v = j == 2 ? T(-2) : (j == 1 || j == 3) ? T(1) : T(0); break;
-        default: break;
-        }
-        S.coef[k][j] = v;
-    }
-
-    // in-plane source offsets of the elements this thread copies (-1 = outside a wall)
-    long long goff[kElemsPerThread];
+    // Copy plan.  Field boxes are kBY rows of FCH 16-byte chunks, the code box kBY rows
+    // of CCH chunks; chunk starts are multiples of 4 cells (nx % 4 == 0), so a chunk
+    // wraps around a periodic boundary as a whole.  fo / co: in-plane element offset of
+    // this thread's field / code chunk (-1: none or outside a wall), fs / cs: its place
+    // in the box.
+    constexpr int FE = 16 / (int)sizeof(T), FCH = kBX / FE, CCH = kBX / 4;
+    int fo[2] = {-1, -1}, fs[2] = {0, 0};
 #pragma unroll
-    for (int s = 0; s < kElemsPerThread; ++s) {
-        const int e = tid + s * kNT;
-        goff[s] = -1;
-        if (e < kPL) {
-            const int hx = e % kHX, hy = e / kHX;
-            const int gx = nb_coord(x0 - 2 + hx, nx, B.per[0]);
-            const int gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
-            if (gx >= 0 && gy >= 0) goff[s] = (long long)gx + (long long)nx * gy;
+    for (int r = 0; r < 2; ++r) {
+        const int c = tid + r * kNT;
+        if (c < FCH * kBY) {
+            const int hy = c / FCH, hx = (c % FCH) * FE;
+            fs[r] = hy * kBX + hx;
+            const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
+            if (gx >= 0 && gy >= 0) fo[r] = gx + nx * gy;
         }
+    }
+    int co = -1, cs = 0;
+    if (tid < CCH * kBY) {
+        const int hy = tid / CCH, hx = (tid % CCH) * 4;
+        cs = hy * kBX + hx;
+        const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
+        if (gx >= 0 && gy >= 0) co = gx + nx * gy;
     }
     auto issue_plane = [&](int k) {
-        const int slot = ring(k);
+        const int slot = ((k % kStages) + kStages) % kStages;
         const int gz = nb_coord(k, nz, B.per[2]);
+        const long long po = (long long)gz * plane;
 #pragma unroll
-        for (int s = 0; s < kElemsPerThread; ++s) {
-            const int e = tid + s * kNT;
-            if (e >= kPL) continue;
-            if (gz >= 0 && goff[s] >= 0) {
-                const long long o = (long long)gz * plane + goff[s];
-                cp_async_elem(&S.ux[slot][e], gux + o);
-                cp_async_elem(&S.uy[slot][e], guy + o);
-                cp_async_elem(&S.uz[slot][e], guz + o);
-                cp_async_elem(&S.pin[slot][e], gp + o);
-                cp_async_elem(&S.cd[slot][e], code + o);
+        for (int r = 0; r < 2; ++r) {
+            if (tid + r * kNT >= FCH * kBY) continue;
+            const int e = fs[r];
+            if (gz >= 0 && fo[r] >= 0) {
+                const long long o = po + fo[r];
+                cp_async16(&S.ux[slot][e], gux + o);
+                cp_async16(&S.uy[slot][e], guy + o);
+                cp_async16(&S.uz[slot][e], guz + o);
+                cp_async16(&S.pin[slot][e], gp + o);
             } else {
-                S.ux[slot][e] = T(0);
-                S.uy[slot][e] = T(0);
-                S.uz[slot][e] = T(0);
-                S.pin[slot][e] = T(0);
-                S.cd[slot][e] = 0u;
+#pragma unroll
+                for (int j = 0; j < FE; ++j) {
+                    S.ux[slot][e + j] = T(0);
+                    S.uy[slot][e + j] = T(0);
+                    S.uz[slot][e + j] = T(0);
+                    S.pin[slot][e + j] = T(0);
+                }
             }
+        }
+        if (tid < CCH * kBY) {
+            if (gz >= 0 && co >= 0) cp_async16(&S.cd[slot][cs], code + po + co);
+            else
+                for (int j = 0; j < 4; ++j) S.cd[slot][cs + j] = 0u;
         }
         cp_async_commit();
     };
 
-    const int own = (ty + 2) * kHX + (tx + 2);
+    const int own = (ty + 2) * kBX + (tx + 4);
     const int gx_own = x0 + tx, gy_own = y0 + ty;
     const bool real = gx_own < nx && gy_own < ny;
     const long long gin_own = (long long)gx_own + (long long)nx * gy_own;
@@ -204,14 +218,13 @@ __global__ void __launch_bounds__(kNT, 2)
         const int wx = nb_coord(gx_own, nx, B.per[0]), wy = nb_coord(gy_own, ny, B.per[1]);
         if (wx >= 0 && wy >= 0) gin_wrap = (long long)wx + (long long)nx * wy;
     }
-
     // halo p^n cells: column x0+TX (rows of the tile) and row y0+TY (columns of the tile)
     const bool halo = tid < kTX + kTY;
-    const int hsx = tid < kTY ? kTX + 2 : (tid - kTY) + 2;
+    const int hsx = tid < kTY ? kTX + 4 : (tid - kTY) + 4;
     const int hsy = tid < kTY ? tid + 2 : kTY + 2;
     long long hg = -1;
-    if (halo && (SRC)) {
-        const int gx = nb_coord(x0 + hsx - 2, nx, B.per[0]), gy = nb_coord(y0 + hsy - 2, ny, B.per[1]);
+    if (halo && SRC) {
+        const int gx = nb_coord(x0 + hsx - 4, nx, B.per[0]), gy = nb_coord(y0 + hsy - 2, ny, B.per[1]);
         if (gx >= 0 && gy >= 0) hg = (long long)gx + (long long)nx * gy;
     }
 
@@ -226,14 +239,14 @@ __global__ void __launch_bounds__(kNT, 2)
     issue_plane(t0 + 1);
     issue_plane(t0 + 2);
 
-    // p^n at smem position e on plane k (slots sk, skm = plane k-1), global in-plane index g
+    // p^n at box position e on plane k (ring slots sk, skm = plane k-1), in-plane index g
     auto pressure = [&](int e, int sk, int skm, int k, long long g, T &div_out) -> T {
         const uint32_t c = S.cd[sk][e];
         div_out = T(0);
         if (!(c & 1u)) return T(0);
         const T p0 = S.pin[sk][e];
         if (MODE == kModeU) return p0;
-        const T dv = (S.ux[sk][e] - S.ux[sk][e - 1]) + (S.uy[sk][e] - S.uy[sk][e - kHX]) +
+        const T dv = (S.ux[sk][e] - S.ux[sk][e - 1]) + (S.uy[sk][e] - S.uy[sk][e - kBX]) +
                      (S.uz[sk][e] - S.uz[skm][e]);
         div_out = dv;
         T rp = T(0);
@@ -244,11 +257,12 @@ __global__ void __launch_bounds__(kNT, 2)
         return p0 - B.dtc2 * (dv - rp);
     };
 
+    int st2 = ((t0 - 2) % kStages + kStages) % kStages;  // ring slots of planes t-2, t-1, t
+    int st1 = (st2 + 1) % kStages, st = (st2 + 2) % kStages;
     for (int t = t0; t <= m1 + 1; ++t) {
         cp_async_wait<2>();
         __syncthreads();
         issue_plane(t + 3);
-        const int st = ring(t), st1 = ring(t - 1), st2 = ring(t - 2);
         // z queues of the own column
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -269,14 +283,17 @@ __global__ void __launch_bounds__(kNT, 2)
             if (REDUCE && real && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) acc[3] += (double)dv * (double)dv;
             if (halo) {
                 T dh;
-                const int e = hsy * kHX + hsx;
+                const int e = hsy * kBX + hsx;
                 S.pn[(t - 1) & 1][e] = pressure(e, st1, st2, t - 1, hg, dh);
             }
         }
         const int m = t - 2;
+        const int sm = st2;
+        st2 = st1;
+        st1 = st;
+        st = st == kStages - 1 ? 0 : st + 1;
         if (m < m0 || !real) continue;
         // ---------------------------------------------------------- update on plane m
-        const int sm = st2;
         const long long gidx = (long long)m * plane + gin_own;
         T un[3];
         if (MODE == kModeP) {
@@ -286,20 +303,14 @@ __global__ void __launch_bounds__(kNT, 2)
         } else {
             const uint32_t c = S.cd[sm][own];
             const T *PN = S.pn[m & 1];
-            const T grad[3] = {PN[own + 1] - pn_prev, PN[own + kHX] - pn_prev, pn_cur - pn_prev};
             const T *ux = S.ux[sm], *uy = S.uy[sm], *uz = S.uz[sm];
-            // perpendicular second derivative (Appendix B) with coefficients of case k
-            auto perp = [&](uint32_t k, T a, T b, T u0, T d, T e) -> T {
-                const T *cf = S.coef[k];
-                return cf[0] * a + cf[1] * b + cf[2] * u0 + cf[3] * d + cf[4] * e;
-            };
-            // u_x: axial x, perpendicular y (smem) and z (queue)
+            // u_x: along x (box), across y (box) and z (queue)
             {
                 const T u0 = qx[2];
                 T lap = ux[own + 1] - T(2) * u0 + ux[own - 1];
-                lap += perp((c >> code_shift(0, 1)) & 7u, ux[own - 2 * kHX], ux[own - kHX], u0, ux[own + kHX],
-                            ux[own + 2 * kHX]);
-                lap += perp((c >> code_shift(0, 2)) & 7u, qx[0], qx[1], u0, qx[3], qx[4]);
+                lap += perp_code((c >> code_shift(0, 1)) & 7u, ux[own - 2 * kBX], ux[own - kBX], u0, ux[own + kBX],
+                                 ux[own + 2 * kBX]);
+                lap += perp_code((c >> code_shift(0, 2)) & 7u, qx[0], qx[1], u0, qx[3], qx[4]);
                 un[0] = u0;
                 if (c & node_bit(0)) {
                     if (B.alpha) {
@@ -307,17 +318,17 @@ __global__ void __launch_bounds__(kNT, 2)
                                              (long long)nb_coord(gx_own + 1, nx, B.per[0]) + (long long)nx * gy_own;
                         lap -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0;
                     }
-                    T R = B.inv_re * lap - grad[0] + P.f[0];
+                    T R = B.inv_re * lap - (PN[own + 1] - pn_prev) + P.f[0];
                     if (SRC) R += P.src[gidx];
                     un[0] = u0 + B.dt * R;
                 }
             }
-            // u_y: axial y, perpendicular x (smem) and z (queue)
+            // u_y: along y (box), across x (box) and z (queue)
             {
                 const T u0 = qy[2];
-                T lap = uy[own + kHX] - T(2) * u0 + uy[own - kHX];
-                lap += perp((c >> code_shift(1, 0)) & 7u, uy[own - 2], uy[own - 1], u0, uy[own + 1], uy[own + 2]);
-                lap += perp((c >> code_shift(1, 2)) & 7u, qy[0], qy[1], u0, qy[3], qy[4]);
+                T lap = uy[own + kBX] - T(2) * u0 + uy[own - kBX];
+                lap += perp_code((c >> code_shift(1, 0)) & 7u, uy[own - 2], uy[own - 1], u0, uy[own + 1], uy[own + 2]);
+                lap += perp_code((c >> code_shift(1, 2)) & 7u, qy[0], qy[1], u0, qy[3], qy[4]);
                 un[1] = u0;
                 if (c & node_bit(1)) {
                     if (B.alpha) {
@@ -325,40 +336,38 @@ __global__ void __launch_bounds__(kNT, 2)
                                              (long long)nx * nb_coord(gy_own + 1, ny, B.per[1]);
                         lap -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0;
                     }
-                    T R = B.inv_re * lap - grad[1] + P.f[1];
+                    T R = B.inv_re * lap - (PN[own + kBX] - pn_prev) + P.f[1];
                     if (SRC) R += P.src[N + gidx];
                     un[1] = u0 + B.dt * R;
                 }
             }
-            // u_z: axial z (queue), perpendicular x and y (smem)
+            // u_z: along z (queue), across x and y (box)
             {
                 const T u0 = qz[1];
                 T lap = qz[2] - T(2) * u0 + qz[0];
-                lap += perp((c >> code_shift(2, 0)) & 7u, uz[own - 2], uz[own - 1], u0, uz[own + 1], uz[own + 2]);
-                lap += perp((c >> code_shift(2, 1)) & 7u, uz[own - 2 * kHX], uz[own - kHX], u0, uz[own + kHX],
-                            uz[own + 2 * kHX]);
+                lap += perp_code((c >> code_shift(2, 0)) & 7u, uz[own - 2], uz[own - 1], u0, uz[own + 1], uz[own + 2]);
+                lap += perp_code((c >> code_shift(2, 1)) & 7u, uz[own - 2 * kBX], uz[own - kBX], u0, uz[own + kBX],
+                                 uz[own + 2 * kBX]);
                 un[2] = u0;
                 if (c & node_bit(2)) {
                     if (B.alpha) {
                         const long long g2 = (long long)nb_coord(m + 1, nz, B.per[2]) * plane + gin_own;
                         lap -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0;
                     }
-                    T R = B.inv_re * lap - grad[2] + P.f[2];
+                    T R = B.inv_re * lap - (pn_cur - pn_prev) + P.f[2];
                     if (SRC) R += P.src[2 * N + gidx];
                     un[2] = u0 + B.dt * R;
                 }
             }
         }
-        {
-            P.uout[gidx] = un[0];
-            P.uout[N + gidx] = un[1];
-            P.uout[2 * N + gidx] = un[2];
-            P.pout[gidx] = pn_prev;
-            if (REDUCE) {
-                acc[0] += (double)un[0];
-                acc[1] += (double)un[1];
-                acc[2] += (double)un[2];
-            }
+        P.uout[gidx] = un[0];
+        P.uout[N + gidx] = un[1];
+        P.uout[2 * N + gidx] = un[2];
+        P.pout[gidx] = pn_prev;
+        if (REDUCE) {
+            acc[0] += (double)un[0];
+            acc[1] += (double)un[1];
+            acc[2] += (double)un[2];
         }
     }
     cp_async_wait<0>();
@@ -390,15 +399,18 @@ inline TiledShape tiled_shape(int nx, int ny, int nz) {
     s.tiles_y = (ny + kTY - 1) / kTY;
     // z chunks: long enough to amortise the 4-plane start-up, enough CTAs to fill the GPU
     int zc = 64;
-    while (zc > 8 && (long long)s.tiles_x * s.tiles_y * ((nz + zc - 1) / zc) < 152 * 8) zc /= 2;
+    while (zc > 8 && (long long)s.tiles_x * s.tiles_y * ((nz + zc - 1) / zc) < 152 * 6) zc /= 2;
     s.zchunk = zc < nz ? zc : nz;
     s.nzc = (nz + s.zchunk - 1) / s.zchunk;
     return s;
 }
 
+// The tiled kernel copies whole 16-byte chunks of 4 cells: x extents must be multiples
+// of 4 (the simple kernel serves the other shapes); in-plane offsets are 32-bit.
 template <typename T>
 inline bool tiled_supported(int nx, int ny, int nz, int nprob) {
-    return nx >= 1 && ny >= 1 && nz >= 1 && nprob >= 1 && nprob <= kMaxBatch;
+    return nx >= 4 && nx % 4 == 0 && ny >= 1 && nz >= 1 && nprob >= 1 && nprob <= kMaxBatch &&
+           (long long)nx * ny < (1ll << 31);
 }
 
 template <typename T>

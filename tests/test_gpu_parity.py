@@ -55,13 +55,18 @@ def _oracle_iterate(oracle_mod, mask, n, drive_dir, bc=(0, 0, 0), U0=None, p0=No
     return U, p
 
 
+# shapes are (nz, ny, nx); the tiled kernel takes nx % 4 == 0 (ragged tiles included),
+# the simple kernel every other shape
 CASES = [
     ("odd_random", lambda: G.random_blocks((5, 7, 9), 0.3, seed=1), (0, 0, 0)),
-    ("spheres_ragged", lambda: G.overlapping_spheres((11, 13, 37), 2.5, 0.6, seed=2), (0, 0, 0)),
+    ("spheres_ragged", lambda: G.overlapping_spheres((11, 13, 36), 2.5, 0.6, seed=2), (0, 0, 0)),
+    ("spheres_2tiles", lambda: G.overlapping_spheres((9, 21, 68), 3.0, 0.6, seed=9), (0, 0, 0)),
     ("walls_y", lambda: G.overlapping_spheres((8, 10, 12), 2.0, 0.7, seed=3), (0, 1, 0)),
-    ("walls_xz", lambda: G.random_blocks((6, 9, 33), 0.25, seed=4), (1, 0, 1)),
+    ("walls_xz", lambda: G.random_blocks((6, 9, 44), 0.25, seed=4), (1, 0, 1)),
+    ("walls_xyz", lambda: G.random_blocks((7, 10, 40), 0.2, seed=10), (1, 1, 1)),
     ("thin_n1", lambda: G.random_blocks((1, 12, 40), 0.3, seed=5), (0, 0, 0)),
-    ("thin_n2", lambda: G.random_blocks((2, 3, 17), 0.2, seed=6), (0, 0, 0)),
+    ("thin_n2", lambda: G.random_blocks((2, 3, 16), 0.2, seed=6), (0, 0, 0)),
+    ("odd_walls", lambda: G.random_blocks((4, 5, 17), 0.2, seed=7), (0, 1, 1)),
 ]
 
 
@@ -153,3 +158,25 @@ def test_no_fluid_is_an_error(api):
     with pytest.raises(api.PMError) as e:
         api.solve_direction(np.ones((4, 4, 4), dtype=np.uint8), 0)
     assert e.value.status == api.PM_ERR_NO_FLUID
+
+
+@pytest.mark.slow
+def test_config2_full_size_batched_launch(api, oracle_mod):
+    """256^3 benchmark geometry in the benchmark's launch configuration (three drives
+    batched per sweep, FP32 fields, graph windows): after exactly 21 iterations
+    (max_iter stops it) the mean velocities of each drive match the oracle's after the
+    same 21 iterations."""
+    mask, _ = G.rsa_sphere_pack((256, 256, 256), 10.0, 0.3, 4.0, 25.0, 0.38, seed=2)
+    r = api.permeability_tensor(torch.from_numpy(mask).cuda(), tol=1e-12, check_every=10, max_iter=21)
+    assert r["status"] == api.PM_ERR_NOT_CONVERGED
+    assert all(s["iters"] == 21 for s in r["stats"])
+    dom = oracle_mod.Domain(mask)
+    dt = api.time_step()
+    K = np.zeros((3, 3))
+    for j in range(3):
+        U, p = dom.zeros()
+        dom.iterate(U, p, 21, drive_dir=j, dt=dt)
+        K[:, j] = dom.mean_velocity(U) / oracle_mod.RE_PAPER
+    scale = np.abs(np.diag(K)).max()
+    np.testing.assert_allclose(r["k_raw"], K, rtol=0, atol=1e-5 * scale)
+    np.testing.assert_allclose(np.diag(r["k_raw"]), np.diag(K), rtol=1e-5)
