@@ -61,7 +61,8 @@ typedef enum pm_status {
     PM_ERR_OOM = 6,             /* device allocation failed */
     PM_ERR_CUDA = 7,            /* any other CUDA runtime error */
     PM_ERR_TIMEOUT = 8,         /* a bounded device wait ran out */
-    PM_ERR_UNSUPPORTED = 9      /* option combination not implemented */
+    PM_ERR_UNSUPPORTED = 9,     /* option combination not implemented */
+    PM_ERR_TOO_LARGE = 10       /* domain exceeds pm_iterate_noalloc's fixed scratch */
 } pm_status;
 
 enum { PM_BC_PERIODIC = 0, PM_BC_WALL = 1 };
@@ -139,6 +140,25 @@ PM_API double pm_time_step(const pm_options *opt);
  *   Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA. */
 PM_API int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_options *opt, int64_t n,
                void *u, void *p, void *cuda_stream);
+
+/* pm_iterate without any device memory allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- for example code running
+ * under another allocator that has already reserved the GPU's memory (a framework's
+ * caching allocator), or a latency-critical loop in which cudaMalloc / cudaFree would
+ * synchronise the device.
+ *   Same arguments, units, results and errors as pm_iterate; u and p are updated in place.
+ *   Limit: nx * ny * nz <= 131072 cells (e.g. 64 x 64 x 32), else PM_ERR_TOO_LARGE.
+ *   Scratch: a fixed 5 MB device array inside the library (a copy of the mask, the
+ *   neighbourhood codes and the second field buffer).  Every GPU that loads the library
+ *   holds it until the process exits.  The first call on a device looks up its device
+ *   address (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (other streams,
+ *   other host threads) race and corrupt each other; serialise them.  Each call
+ *   rewrites every scratch value it reads, so nothing carries over between calls.
+ *   The call runs on cuda_stream itself and returns after it has finished. */
+PM_API int pm_iterate_noalloc(const pm_domain *dom, int dir, double drive, const pm_options *opt, int64_t n,
+                              void *u, void *p, void *cuda_stream);
 
 /* One drive direction to convergence (Algorithm 1, Sec. 4 "Permeability computation").
  *   dir: 0, 1, 2 = drive along e_1, e_2, e_3 (case a, b, c of Eq. cases_pressure).

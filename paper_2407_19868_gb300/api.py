@@ -24,6 +24,7 @@ PM_ERR_OOM = 6
 PM_ERR_CUDA = 7
 PM_ERR_TIMEOUT = 8
 PM_ERR_UNSUPPORTED = 9
+PM_ERR_TOO_LARGE = 10
 
 PERIODIC = 0
 WALL = 1
@@ -36,7 +37,7 @@ _PRECISION = {"fp32": FP32_RED64, "fp32_red64": FP32_RED64, "fp32_dc64": FP32_DC
 
 # every function the header declares (checked by the ABI test)
 EXPORTED = ["pm_default_options", "pm_strerror", "pm_version", "pm_time_step", "pm_iterate",
-            "pm_solve_direction", "pm_permeability_tensor"]
+            "pm_iterate_noalloc", "pm_solve_direction", "pm_permeability_tensor"]
 
 
 class PMError(RuntimeError):
@@ -101,6 +102,7 @@ def load():
         L.pm_time_step.argtypes = [C.POINTER(Options)]
         L.pm_iterate.argtypes = [C.POINTER(Domain), C.c_int, C.c_double, C.POINTER(Options), C.c_int64,
                                  vp, vp, vp]
+        L.pm_iterate_noalloc.argtypes = L.pm_iterate.argtypes
         L.pm_solve_direction.argtypes = [C.POINTER(Domain), C.c_int, C.c_double, C.POINTER(Options),
                                          vp, vp, vp, vp, dp, C.POINTER(Stats), vp]
         L.pm_permeability_tensor.argtypes = [C.POINTER(Domain), C.c_double, C.POINTER(Options), dp, dp,

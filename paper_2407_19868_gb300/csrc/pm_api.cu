@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/poremaps_gb.h"
@@ -637,6 +639,109 @@ int tensor_like(const pm_domain *dom, const pm_options *o, int ndirs, const int 
     return status;
 }
 
+// ------------------------------------------------------------------ allocation-free iterate
+// Fixed scratch of pm_iterate_noalloc: a copy of the mask, the neighbourhood flags and
+// stencil codes, and the second buffer of the ping-pong pair (FP64 worst case).  It is
+// a file-scope device array, so it exists on every GPU that loads the library until the
+// process exits, and all calls share it.
+constexpr long long kNoAllocMaxCells = 1ll << 17;
+constexpr size_t kNoAllocBytes = (size_t)kNoAllocMaxCells * (1 + 1 + 4 + 4 * sizeof(double)) + 8 * 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of the scratch on the current device.  Host code only sees a host-side
+// stand-in under the array's name, so the address is looked up once per device (with
+// that device current) and cached.
+int noalloc_scratch(unsigned char **out) {
+    static std::mutex mu;
+    static unsigned char *addr[256] = {};
+    int dev = 0;
+    PM_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return PM_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return map_cuda(e);
+        }
+        addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = addr[dev];
+    return PM_OK;
+}
+
+template <typename T>
+int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_options *o, int64_t n, T *u, T *p,
+                         cudaStream_t s, unsigned char *scr) {
+    const long long N = (long long)dom->nx * dom->ny * dom->nz;
+    auto carve = [&](size_t bytes) {
+        unsigned char *q = scr;
+        scr += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    uint8_t *mask = carve((size_t)N);
+    uint8_t *flags = carve((size_t)N);
+    uint32_t *code = reinterpret_cast<uint32_t *>(carve(4 * (size_t)N));
+    T *u2 = reinterpret_cast<T *>(carve(3 * sizeof(T) * (size_t)N));
+    T *p2 = reinterpret_cast<T *>(carve(sizeof(T) * (size_t)N));
+    const int per[3] = {dom->bc[0] == PM_BC_PERIODIC, dom->bc[1] == PM_BC_PERIODIC, dom->bc[2] == PM_BC_PERIODIC};
+    PM_CK(cudaMemcpyAsync(mask, dom->mask, (size_t)N, dom->mask_on_device ? cudaMemcpyDeviceToDevice
+                                                                          : cudaMemcpyHostToDevice, s));
+    classify_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], flags);
+    code_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], code);
+    sanitize_kernel<T><<<launch_grid(N), 256, 0, s>>>(flags, N, u, p);
+    PM_CK(cudaGetLastError());
+    if (n == 0) return PM_OK;
+    const double dts = time_step(o);
+    SweepBatch<T> B{};
+    B.nx = dom->nx;
+    B.ny = dom->ny;
+    B.nz = dom->nz;
+    for (int a = 0; a < 3; ++a) B.per[a] = per[a];
+    B.N = N;
+    B.flags = flags;
+    B.alpha = nullptr;
+    B.inv_re = (T)(1.0 / o->Re);
+    B.dt = (T)dts;
+    B.dtc2 = (T)(dts * o->c2);
+    B.nprob = 1;
+    for (int d = 0; d < 3; ++d) B.prob[0].f[d] = (T)(d == dir ? drive : 0.0);
+    // ping-pong between the caller's fields (buffer 0) and the scratch (buffer 1)
+    T *ub[2] = {u, u2}, *pb[2] = {p, p2};
+    int cur = 0;
+    auto step = [&](int mode) -> int {
+        B.prob[0].uin = ub[cur];
+        B.prob[0].pin = pb[cur];
+        B.prob[0].uout = ub[1 - cur];
+        B.prob[0].pout = pb[1 - cur];
+        B.prob[0].src = nullptr;
+        B.prob[0].partials = nullptr;
+        int st;
+        if (tiled_supported<T>(B.nx, B.ny, B.nz, 1)) {
+            if ((st = launch_tiled<T>(B, code, mode, false, false, s))) return st;
+        } else {
+            dim3 blk(32, 8, 1), grd((B.nx + 31) / 32, (B.ny + 7) / 8, (unsigned)B.nz);
+            if (mode == kModeU) sweep_simple_kernel<T, kModeU, false, false><<<grd, blk, 0, s>>>(B);
+            else if (mode == kModePU) sweep_simple_kernel<T, kModePU, false, false><<<grd, blk, 0, s>>>(B);
+            else sweep_simple_kernel<T, kModeP, false, false><<<grd, blk, 0, s>>>(B);
+        }
+        PM_CK(cudaGetLastError());
+        cur ^= 1;
+        return PM_OK;
+    };
+    int st;
+    if ((st = step(kModeU))) return st;
+    for (int64_t i = 1; i < n; ++i)
+        if ((st = step(kModePU))) return st;
+    if ((st = step(kModeP))) return st;
+    if (cur == 1) {
+        PM_CK(cudaMemcpyAsync(u, u2, 3 * sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+        PM_CK(cudaMemcpyAsync(p, p2, sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+    }
+    return PM_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -671,6 +776,7 @@ const char *pm_strerror(int s) {
     case PM_ERR_CUDA: return "CUDA runtime error";
     case PM_ERR_TIMEOUT: return "bounded device wait ran out";
     case PM_ERR_UNSUPPORTED: return "option combination not supported";
+    case PM_ERR_TOO_LARGE: return "domain larger than the fixed scratch of pm_iterate_noalloc (131072 cells)";
     default: return "unknown status";
     }
 }
@@ -698,6 +804,27 @@ int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_options *o,
     cudaError_t e = cudaStreamSynchronize(ss.s);
     if (!st && e != cudaSuccess) st = map_cuda(e);
     return st;
+}
+
+int pm_iterate_noalloc(const pm_domain *dom, int dir, double drive, const pm_options *o, int64_t n, void *u,
+                       void *p, void *cuda_stream) {
+    int st = validate_domain(dom);
+    if (st) return st;
+    if ((st = validate_options(o))) return st;
+    if (dir < 0 || dir > 2 || !u || !p || n < 0) return PM_ERR_INVALID_ARG;
+    if (o->precision == PM_FP32_DC64) return PM_ERR_INVALID_ARG;
+    if ((long long)dom->nx * dom->ny * dom->nz > kNoAllocMaxCells) return PM_ERR_TOO_LARGE;
+    unsigned char *scr = nullptr;
+    if ((st = noalloc_scratch(&scr))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (o->precision == PM_FP64)
+        st = iterate_noalloc_impl<double>(dom, dir, drive, o, n, (double *)u, (double *)p, s, scr);
+    else
+        st = iterate_noalloc_impl<float>(dom, dir, drive, o, n, (float *)u, (float *)p, s, scr);
+    if (st) return st;
+    // the host mask (if any) is read by an asynchronous copy: finish before returning
+    cudaError_t e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? PM_OK : map_cuda(e);
 }
 
 int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_options *o, float *u, float *p,
