@@ -266,6 +266,21 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """A short run of the sweep kernel on the benchmark mask for ncu captures: one drive,
+    FP32 fields, ``--profile-iters`` iterations through pm_iterate."""
+    import torch
+    from paper_2407_19868_gb300 import api
+    api.load()
+    mask, _ = make_mask()
+    u = torch.zeros((3,) + mask.shape, dtype=torch.float32, device="cuda")
+    p = torch.zeros(mask.shape, dtype=torch.float32, device="cuda")
+    api.iterate(torch.from_numpy(mask).cuda(), u, p, args.profile_iters, drive_dir=0, precision="fp32")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "pm_iterate", "iters": args.profile_iters, "mean_ux": float(u[0].mean())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,7 +293,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=300)
     ap.add_argument("--ref-iters", type=int, default=5)
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling case: run this many pm_iterate iterations (one drive, FP32) on the mask and exit")
     args = ap.parse_args()
+    if args.profile_iters > 0:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -272,7 +272,11 @@ struct Solver {
         inv_re = (T)(1.0 / o.Re);
         dim3 gr = grid();
         nblk = (long long)gr.x * gr.y * g.nz;
-        const long long nblk_t = tiled_num_blocks<T>(g.nx, g.ny, g.nz);
+        long long nblk_t = 0;
+        for (int k = 1; k <= kMaxBatch; ++k) {
+            const long long b = tiled_num_blocks<T>(g.nx, g.ny, g.nz, k);
+            nblk_t = b > nblk_t ? b : nblk_t;
+        }
         const long long nblk_max = nblk > nblk_t ? nblk : nblk_t;
         int st;
         for (int k = 0; k < nprob; ++k) {
@@ -355,8 +359,9 @@ struct Solver {
     }
 
     long long reduce_blocks() const {
-        return (o.kernel == 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob)) ? tiled_num_blocks<T>(g.nx, g.ny, g.nz)
-                                                                            : nblk;
+        return (o.kernel == 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob))
+                   ? tiled_num_blocks<T>(g.nx, g.ny, g.nz, nprob)
+                   : nblk;
     }
 
     int reduce_to_host_async() {

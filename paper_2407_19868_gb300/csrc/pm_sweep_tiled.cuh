@@ -100,38 +100,54 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ------------------------------------------------------------------ kernel
-// Tile TX x TY cells, thread (tx, ty) owns cell (x0 + tx, y0 + ty).  Shared-memory boxes
-// are BX = TX + 8 wide (x0 - 4 .. x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4 high
-// (y0 - 2 .. y0 + TY + 1); the stencil needs +-2 in x and y.
-constexpr int kTX = 32, kTY = 8, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY, kStages = 6;
-constexpr int kNT = kTX * kTY;
+// Tile TX x TY cells, thread (lane, ty) owns the pair of cells (x0 + 2 lane, y0 + ty) and
+// (x0 + 2 lane + 1, y0 + ty).  Shared-memory boxes are BX = TX + 8 wide (x0 - 4 ..
+// x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4 high (y0 - 2 .. y0 + TY + 1); the
+// stencil needs +-2 in x and y.
+constexpr int kTX = 64, kTY = 8, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY, kStages = 6;
+constexpr int kNT = (kTX / 2) * kTY;
+
+// One ring stage: the five arrays of one plane, contiguous, so that every access is a
+// per-step stage pointer plus a compile-time offset.
+template <typename T>
+struct TiledStage {
+    T ux[kPL];
+    T uy[kPL];
+    T uz[kPL];
+    T pin[kPL];
+    uint32_t cd[kPL];
+};
+
+// Wall coefficients per 3-bit code (kind, side): the second derivative across the flow is
+// A (u(-1) + u(+1)) + B u0 + Cm u(-2) + Cp u(+2)  (non-fluid nodes hold 0).
+template <typename T>
+struct alignas(4 * sizeof(T)) WallCoef {
+    T A, B, Cm, Cp;
+};
 
 template <typename T>
 struct TiledSmem {
-    T ux[kStages][kPL];
-    T uy[kStages][kPL];
-    T uz[kStages][kPL];
-    T pin[kStages][kPL];
-    uint32_t cd[kStages][kPL];
+    TiledStage<T> st[kStages];
     T pn[2][kPL];
+    WallCoef<T> coef[8];
 };
 
-// Appendix B second derivative across the flow from the 3-bit wall code (kind, side).
-// Non-fluid nodes hold 0, so u(-1) + u(+1) is the one-sided neighbour when a wall is
-// on the other side.
+// A pair of x-adjacent values (aligned for one 2-wide shared-memory access).
 template <typename T>
-__device__ __forceinline__ T perp_code(uint32_t k3, T um2, T um1, T u0, T up1, T up2) {
-    const uint32_t kind = k3 & 3u;
-    const T v1 = um1 + up1;
-    const T v2 = (k3 & 4u) ? up2 : um2;
-    const T A = kind == 0u ? T(1) : (kind == 2u ? T(2) : T(8) / T(3));
-    const T Bc = kind == 0u ? T(-2) : (kind == 1u ? T(-8) : (kind == 2u ? T(-5) : T(-16) / T(3)));
-    const T C = kind == 2u ? T(-1) / T(5) : T(0);
-    return A * v1 + Bc * u0 + C * v2;
+struct alignas(2 * sizeof(T)) Pair {
+    T a, b;
+};
+template <typename T>
+__device__ __forceinline__ Pair<T> ld2(const T *p) {
+    return *reinterpret_cast<const Pair<T> *>(p);
+}
+template <typename T>
+__device__ __forceinline__ Pair<uint32_t> ld2u(const uint32_t *p) {
+    return *reinterpret_cast<const Pair<uint32_t> *>(p);
 }
 
 template <typename T, int MODE, bool REDUCE, bool SRC>
-__global__ void __launch_bounds__(kNT, 3)
+__global__ void __launch_bounds__(kNT, 2)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int zchunk, int tiles_x,
                        int tiles_y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -139,7 +155,7 @@ __global__ void __launch_bounds__(kNT, 3)
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const long long N = B.N, plane = (long long)nx * ny;
     const int tid = threadIdx.x;
-    const int tx = tid % kTX, ty = tid / kTX;
+    const int lane = tid & 31, ty = tid >> 5;
     const int pi = blockIdx.x % B.nprob;
     const int tile = blockIdx.x / B.nprob;
     const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
@@ -151,17 +167,35 @@ __global__ void __launch_bounds__(kNT, 3)
     const T *__restrict__ guz = P.uin + 2 * N;
     const T *__restrict__ gp = P.pin;
 
+    if (tid < 8) {
+        // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3;
+        // side selects which +-2 node the one-sided cases use
+        const int kind = tid & 3, side = tid >> 2;
+        WallCoef<T> w;
+        w.A = kind == 0 ? T(1) : (kind == 2 ? T(2) : (kind == 3 ? T(8) / T(3) : T(0)));
+        w.B = kind == 0 ? T(-2) : (kind == 1 ? T(-8) : (kind == 2 ? T(-5) : T(-16) / T(3)));
+        const T c = kind == 2 ? T(-1) / T(5) : T(0);
+        w.Cm = side ? T(0) : c;
+        w.Cp = side ? c : T(0);
+        S.coef[tid] = w;
+    }
+
     // Copy plan.  Field boxes are kBY rows of FCH 16-byte chunks, the code box kBY rows
     // of CCH chunks; chunk starts are multiples of 4 cells (nx % 4 == 0), so a chunk
     // wraps around a periodic boundary as a whole.  fo / co: in-plane element offset of
     // this thread's field / code chunk (-1: none or outside a wall), fs / cs: its place
     // in the box.
     constexpr int FE = 16 / (int)sizeof(T), FCH = kBX / FE, CCH = kBX / 4;
-    int fo[2] = {-1, -1}, fs[2] = {0, 0};
+    constexpr int FR = (FCH * kBY + kNT - 1) / kNT;
+    int fo[FR], fs[FR];
+    bool fhas[FR];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < FR; ++r) {
         const int c = tid + r * kNT;
-        if (c < FCH * kBY) {
+        fo[r] = -1;
+        fs[r] = 0;
+        fhas[r] = c < FCH * kBY;
+        if (fhas[r]) {
             const int hy = c / FCH, hx = (c % FCH) * FE;
             fs[r] = hy * kBX + hx;
             const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
@@ -169,47 +203,48 @@ __global__ void __launch_bounds__(kNT, 3)
         }
     }
     int co = -1, cs = 0;
-    if (tid < CCH * kBY) {
+    const bool chas = tid < CCH * kBY;
+    if (chas) {
         const int hy = tid / CCH, hx = (tid % CCH) * 4;
         cs = hy * kBX + hx;
         const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
         if (gx >= 0 && gy >= 0) co = gx + nx * gy;
     }
     auto issue_plane = [&](int k) {
-        const int slot = ((k % kStages) + kStages) % kStages;
+        TiledStage<T> &G = S.st[((k % kStages) + kStages) % kStages];
         const int gz = nb_coord(k, nz, B.per[2]);
         const long long po = (long long)gz * plane;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            if (tid + r * kNT >= FCH * kBY) continue;
+        for (int r = 0; r < FR; ++r) {
+            if (!fhas[r]) continue;
             const int e = fs[r];
             if (gz >= 0 && fo[r] >= 0) {
                 const long long o = po + fo[r];
-                cp_async16(&S.ux[slot][e], gux + o);
-                cp_async16(&S.uy[slot][e], guy + o);
-                cp_async16(&S.uz[slot][e], guz + o);
-                cp_async16(&S.pin[slot][e], gp + o);
+                cp_async16(&G.ux[e], gux + o);
+                cp_async16(&G.uy[e], guy + o);
+                cp_async16(&G.uz[e], guz + o);
+                cp_async16(&G.pin[e], gp + o);
             } else {
 #pragma unroll
                 for (int j = 0; j < FE; ++j) {
-                    S.ux[slot][e + j] = T(0);
-                    S.uy[slot][e + j] = T(0);
-                    S.uz[slot][e + j] = T(0);
-                    S.pin[slot][e + j] = T(0);
+                    G.ux[e + j] = T(0);
+                    G.uy[e + j] = T(0);
+                    G.uz[e + j] = T(0);
+                    G.pin[e + j] = T(0);
                 }
             }
         }
-        if (tid < CCH * kBY) {
-            if (gz >= 0 && co >= 0) cp_async16(&S.cd[slot][cs], code + po + co);
+        if (chas) {
+            if (gz >= 0 && co >= 0) cp_async16(&G.cd[cs], code + po + co);
             else
-                for (int j = 0; j < 4; ++j) S.cd[slot][cs + j] = 0u;
+                for (int j = 0; j < 4; ++j) G.cd[cs + j] = 0u;
         }
         cp_async_commit();
     };
 
-    const int own = (ty + 2) * kBX + (tx + 4);
-    const int gx_own = x0 + tx, gy_own = y0 + ty;
-    const bool real = gx_own < nx && gy_own < ny;
+    const int own = (ty + 2) * kBX + 4 + 2 * lane;  // box index of the first cell of the pair
+    const int gx_own = x0 + 2 * lane, gy_own = y0 + ty;
+    const bool real0 = gx_own < nx && gy_own < ny;       // nx % 4 == 0: both cells or neither
     const long long gin_own = (long long)gx_own + (long long)nx * gy_own;
     // tile positions past the domain edge stand for their periodic image (or for solid
     // outside a wall): their pressure is formed at the wrapped index, nothing is written
@@ -218,20 +253,28 @@ __global__ void __launch_bounds__(kNT, 3)
         const int wx = nb_coord(gx_own, nx, B.per[0]), wy = nb_coord(gy_own, ny, B.per[1]);
         if (wx >= 0 && wy >= 0) gin_wrap = (long long)wx + (long long)nx * wy;
     }
-    // halo p^n cells: column x0+TX (rows of the tile) and row y0+TY (columns of the tile)
-    const bool halo = tid < kTX + kTY;
-    const int hsx = tid < kTY ? kTX + 4 : (tid - kTY) + 4;
-    const int hsy = tid < kTY ? tid + 2 : kTY + 2;
+    // halo p^n: the last warp takes the row y0 + TY (pairs), the last TY lanes of the
+    // warp before it the column x0 + TX (single cells); for FP32 these lanes issue no
+    // copies (216 chunks per array), which balances the work before the barrier
+    const bool hrow = ty == kTY - 1, hcol = ty == kTY - 2 && lane >= 32 - kTY;
+    const int hown = hrow ? (kTY + 2) * kBX + 4 + 2 * lane : (lane - (32 - kTY) + 2) * kBX + kTX + 4;
     long long hg = -1;
-    if (halo && SRC) {
-        const int gx = nb_coord(x0 + hsx - 4, nx, B.per[0]), gy = nb_coord(y0 + hsy - 2, ny, B.per[1]);
+    if ((hrow || hcol) && SRC) {
+        const int gx = nb_coord(x0 + (hown % kBX) - 4, nx, B.per[0]), gy = nb_coord(y0 + hown / kBX - 2, ny, B.per[1]);
         if (gx >= 0 && gy >= 0) hg = (long long)gx + (long long)nx * gy;
     }
+    // offsets to the +x / +y cell for the drag term; at a wall the face is not fluid and the
+    // value is discarded, so the cell itself stands in (keeps the read in bounds)
+    const int wxp = nb_coord(gx_own + 2, nx, B.per[0]), wyp = nb_coord(gy_own + 1, ny, B.per[1]);
+    const long long ex1_off = wxp >= 0 ? (long long)wxp - (gx_own + 1) : 0;  // second cell's +x
+    const long long ey_off = wyp >= 0 ? ((long long)wyp - gy_own) * nx : 0;
 
-    T qx[5] = {T(0), T(0), T(0), T(0), T(0)};
-    T qy[5] = {T(0), T(0), T(0), T(0), T(0)};
-    T qz[3] = {T(0), T(0), T(0)};
-    T pn_prev = T(0), pn_cur = T(0);
+    Pair<T> qx[5], qy[5], qz[3];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) qx[i] = qy[i] = Pair<T>{T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) qz[i] = Pair<T>{T(0), T(0)};
+    Pair<T> pn_prev{T(0), T(0)}, pn_cur{T(0), T(0)};
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 
     const int t0 = m0 - 2;
@@ -239,135 +282,188 @@ __global__ void __launch_bounds__(kNT, 3)
     issue_plane(t0 + 1);
     issue_plane(t0 + 2);
 
-    // p^n at box position e on plane k (ring slots sk, skm = plane k-1), in-plane index g
-    auto pressure = [&](int e, int sk, int skm, int k, long long g, T &div_out) -> T {
-        const uint32_t c = S.cd[sk][e];
-        div_out = T(0);
-        if (!(c & 1u)) return T(0);
-        const T p0 = S.pin[sk][e];
-        if (MODE == kModeU) return p0;
-        const T dv = (S.ux[sk][e] - S.ux[sk][e - 1]) + (S.uy[sk][e] - S.uy[sk][e - kBX]) +
-                     (S.uz[sk][e] - S.uz[skm][e]);
-        div_out = dv;
+    // p^n of one cell at box position e of plane k (stage K), the plane below in KM
+    auto press1 = [&](const TiledStage<T> &K, const TiledStage<T> &KM, int e, int k, long long g) -> T {
+        const T dv = (K.ux[e] - K.ux[e - 1]) + (K.uy[e] - K.uy[e - kBX]) + (K.uz[e] - KM.uz[e]);
         T rp = T(0);
         if (SRC && g >= 0) {
             const int gz = nb_coord(k, nz, B.per[2]);
             if (gz >= 0) rp = P.src[3 * N + (long long)gz * plane + g];
         }
-        return p0 - B.dtc2 * (dv - rp);
+        const T p0 = K.pin[e];
+        const T pn = MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
+        return (K.cd[e] & 1u) ? pn : T(0);
     };
 
-    int st2 = ((t0 - 2) % kStages + kStages) % kStages;  // ring slots of planes t-2, t-1, t
-    int st1 = (st2 + 1) % kStages, st = (st2 + 2) % kStages;
+    int s2 = ((t0 - 2) % kStages + kStages) % kStages;  // ring stages of planes t-2, t-1, t
+    int s1 = (s2 + 1) % kStages, s0 = (s2 + 2) % kStages;
+    T *outx = P.uout + (long long)m0 * plane + gin_own;
+    T *outp = P.pout + (long long)m0 * plane + gin_own;
     for (int t = t0; t <= m1 + 1; ++t) {
         cp_async_wait<2>();
         __syncthreads();
         issue_plane(t + 3);
-        // z queues of the own column
+        const TiledStage<T> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
+        // z queues of the own column pair
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             qx[i] = qx[i + 1];
             qy[i] = qy[i + 1];
         }
-        qx[4] = S.ux[st][own];
-        qy[4] = S.uy[st][own];
+        qx[4] = ld2(&G0.ux[own]);
+        qy[4] = ld2(&G0.uy[own]);
         qz[0] = qz[1];
         qz[1] = qz[2];
-        qz[2] = S.uz[st1][own];
-        // p^n on plane t-1: own cell and halo cells
+        qz[2] = ld2(&G1.uz[own]);
+        // p^n on plane t-1: own pair (its u values are in the queues) and halo cells
         pn_prev = pn_cur;
         {
-            T dv;
-            pn_cur = pressure(own, st1, st2, t - 1, gin_wrap, dv);
-            S.pn[(t - 1) & 1][own] = pn_cur;
-            if (REDUCE && real && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) acc[3] += (double)dv * (double)dv;
-            if (halo) {
-                T dh;
-                const int e = hsy * kBX + hsx;
-                S.pn[(t - 1) & 1][e] = pressure(e, st1, st2, t - 1, hg, dh);
+            const Pair<uint32_t> cd = ld2u<T>(&G1.cd[own]);
+            const Pair<T> pin = ld2(&G1.pin[own]);
+            const Pair<T> uyd = ld2(&G1.uy[own - kBX]);
+            const T uxl = G1.ux[own - 1];
+            T dv0 = (qx[3].a - uxl) + (qy[3].a - uyd.a) + (qz[2].a - qz[1].a);
+            T dv1 = (qx[3].b - qx[3].a) + (qy[3].b - uyd.b) + (qz[2].b - qz[1].b);
+            T rp0 = T(0), rp1 = T(0);
+            if (SRC && gin_wrap >= 0) {
+                const int gz = nb_coord(t - 1, nz, B.per[2]);
+                if (gz >= 0) {
+                    const Pair<T> r = ld2(P.src + 3 * N + (long long)gz * plane + gin_wrap);
+                    rp0 = r.a;
+                    rp1 = r.b;
+                }
+            }
+            const bool pore0 = cd.a & 1u, pore1 = cd.b & 1u;
+            pn_cur.a = pore0 ? (MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0)) : T(0);
+            pn_cur.b = pore1 ? (MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1)) : T(0);
+            *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own]) = pn_cur;
+            if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) {
+                dv0 = pore0 ? dv0 : T(0);
+                dv1 = pore1 ? dv1 : T(0);
+                acc[3] += (double)dv0 * (double)dv0 + (double)dv1 * (double)dv1;
+            }
+            if (hrow) {
+                T *dst = &S.pn[(t - 1) & 1][hown];
+                dst[0] = press1(G1, G2, hown, t - 1, hg);
+                dst[1] = press1(G1, G2, hown + 1, t - 1, hg >= 0 ? hg + 1 : -1);
+            } else if (hcol) {
+                S.pn[(t - 1) & 1][hown] = press1(G1, G2, hown, t - 1, hg);
             }
         }
         const int m = t - 2;
-        const int sm = st2;
-        st2 = st1;
-        st1 = st;
-        st = st == kStages - 1 ? 0 : st + 1;
-        if (m < m0 || !real) continue;
+        s2 = s1;
+        s1 = s0;
+        s0 = s0 == kStages - 1 ? 0 : s0 + 1;
+        if (m < m0 || !real0) continue;
         // ---------------------------------------------------------- update on plane m
-        const long long gidx = (long long)m * plane + gin_own;
-        T un[3];
+        Pair<T> ux_n, uy_n, uz_n;
         if (MODE == kModeP) {
-            un[0] = qx[2];
-            un[1] = qy[2];
-            un[2] = qz[1];
+            ux_n = qx[2];
+            uy_n = qy[2];
+            uz_n = qz[1];
         } else {
-            const uint32_t c = S.cd[sm][own];
+            const Pair<uint32_t> c = ld2u<T>(&G2.cd[own]);
             const T *PN = S.pn[m & 1];
-            const T *ux = S.ux[sm], *uy = S.uy[sm], *uz = S.uz[sm];
+            const T *ux = G2.ux, *uy = G2.uy, *uz = G2.uz;
+            // second derivative across the flow (Appendix B) from the 3-bit wall code
+            auto perp = [&](uint32_t cc, int shift, T um2, T um1, T u0, T up1, T up2) -> T {
+                const WallCoef<T> w = S.coef[(cc >> shift) & 7u];
+                return w.A * (um1 + up1) + w.B * u0 + w.Cm * um2 + w.Cp * up2;
+            };
+            const long long gidx = (long long)m * plane + gin_own;
+            const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
             // u_x: along x (box), across y (box) and z (queue)
             {
-                const T u0 = qx[2];
-                T lap = ux[own + 1] - T(2) * u0 + ux[own - 1];
-                lap += perp_code((c >> code_shift(0, 1)) & 7u, ux[own - 2 * kBX], ux[own - kBX], u0, ux[own + kBX],
-                                 ux[own + 2 * kBX]);
-                lap += perp_code((c >> code_shift(0, 2)) & 7u, qx[0], qx[1], u0, qx[3], qx[4]);
-                un[0] = u0;
-                if (c & node_bit(0)) {
-                    if (B.alpha) {
-                        const long long g2 = (long long)m * plane +
-                                             (long long)nb_coord(gx_own + 1, nx, B.per[0]) + (long long)nx * gy_own;
-                        lap -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0;
-                    }
-                    T R = B.inv_re * lap - (PN[own + 1] - pn_prev) + P.f[0];
-                    if (SRC) R += P.src[gidx];
-                    un[0] = u0 + B.dt * R;
+                const Pair<T> u0 = qx[2];
+                const Pair<T> L = ld2(&ux[own - 2]), R = ld2(&ux[own + 2]);
+                const Pair<T> ym2 = ld2(&ux[own - 2 * kBX]), ym1 = ld2(&ux[own - kBX]);
+                const Pair<T> yp1 = ld2(&ux[own + kBX]), yp2 = ld2(&ux[own + 2 * kBX]);
+                T lap0 = u0.b - T(2) * u0.a + L.b;
+                T lap1 = R.a - T(2) * u0.b + u0.a;
+                lap0 += perp(c.a, code_shift(0, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
+                lap1 += perp(c.b, code_shift(0, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
+                lap0 += perp(c.a, code_shift(0, 2), qx[0].a, qx[1].a, u0.a, qx[3].a, qx[4].a);
+                lap1 += perp(c.b, code_shift(0, 2), qx[0].b, qx[1].b, u0.b, qx[3].b, qx[4].b);
+                if (B.alpha) {
+                    lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + 1]) * u0.a;
+                    lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ex1_off]) * u0.b;
                 }
+                const T pr = PN[own + 2];
+                T R0 = B.inv_re * lap0 - (pn_prev.b - pn_prev.a) + fx;
+                T R1 = B.inv_re * lap1 - (pr - pn_prev.b) + fx;
+                if (SRC) {
+                    const Pair<T> sx = ld2(P.src + gidx);
+                    R0 += sx.a;
+                    R1 += sx.b;
+                }
+                ux_n.a = (c.a & node_bit(0)) ? u0.a + B.dt * R0 : u0.a;
+                ux_n.b = (c.b & node_bit(0)) ? u0.b + B.dt * R1 : u0.b;
             }
             // u_y: along y (box), across x (box) and z (queue)
             {
-                const T u0 = qy[2];
-                T lap = uy[own + kBX] - T(2) * u0 + uy[own - kBX];
-                lap += perp_code((c >> code_shift(1, 0)) & 7u, uy[own - 2], uy[own - 1], u0, uy[own + 1], uy[own + 2]);
-                lap += perp_code((c >> code_shift(1, 2)) & 7u, qy[0], qy[1], u0, qy[3], qy[4]);
-                un[1] = u0;
-                if (c & node_bit(1)) {
-                    if (B.alpha) {
-                        const long long g2 = (long long)m * plane + (long long)gx_own +
-                                             (long long)nx * nb_coord(gy_own + 1, ny, B.per[1]);
-                        lap -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0;
-                    }
-                    T R = B.inv_re * lap - (PN[own + kBX] - pn_prev) + P.f[1];
-                    if (SRC) R += P.src[N + gidx];
-                    un[1] = u0 + B.dt * R;
+                const Pair<T> u0 = qy[2];
+                const Pair<T> L = ld2(&uy[own - 2]), R = ld2(&uy[own + 2]);
+                const Pair<T> ym1 = ld2(&uy[own - kBX]), yp1 = ld2(&uy[own + kBX]);
+                T lap0 = yp1.a - T(2) * u0.a + ym1.a;
+                T lap1 = yp1.b - T(2) * u0.b + ym1.b;
+                lap0 += perp(c.a, code_shift(1, 0), L.a, L.b, u0.a, u0.b, R.a);
+                lap1 += perp(c.b, code_shift(1, 0), L.b, u0.a, u0.b, R.a, R.b);
+                lap0 += perp(c.a, code_shift(1, 2), qy[0].a, qy[1].a, u0.a, qy[3].a, qy[4].a);
+                lap1 += perp(c.b, code_shift(1, 2), qy[0].b, qy[1].b, u0.b, qy[3].b, qy[4].b);
+                if (B.alpha) {
+                    lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + ey_off]) * u0.a;
+                    lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ey_off]) * u0.b;
                 }
+                const Pair<T> pny = ld2(&PN[own + kBX]);
+                T R0 = B.inv_re * lap0 - (pny.a - pn_prev.a) + fy;
+                T R1 = B.inv_re * lap1 - (pny.b - pn_prev.b) + fy;
+                if (SRC) {
+                    const Pair<T> sy = ld2(P.src + N + gidx);
+                    R0 += sy.a;
+                    R1 += sy.b;
+                }
+                uy_n.a = (c.a & node_bit(1)) ? u0.a + B.dt * R0 : u0.a;
+                uy_n.b = (c.b & node_bit(1)) ? u0.b + B.dt * R1 : u0.b;
             }
             // u_z: along z (queue), across x and y (box)
             {
-                const T u0 = qz[1];
-                T lap = qz[2] - T(2) * u0 + qz[0];
-                lap += perp_code((c >> code_shift(2, 0)) & 7u, uz[own - 2], uz[own - 1], u0, uz[own + 1], uz[own + 2]);
-                lap += perp_code((c >> code_shift(2, 1)) & 7u, uz[own - 2 * kBX], uz[own - kBX], u0, uz[own + kBX],
-                                 uz[own + 2 * kBX]);
-                un[2] = u0;
-                if (c & node_bit(2)) {
-                    if (B.alpha) {
-                        const long long g2 = (long long)nb_coord(m + 1, nz, B.per[2]) * plane + gin_own;
-                        lap -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0;
-                    }
-                    T R = B.inv_re * lap - (pn_cur - pn_prev) + P.f[2];
-                    if (SRC) R += P.src[2 * N + gidx];
-                    un[2] = u0 + B.dt * R;
+                const Pair<T> u0 = qz[1];
+                const Pair<T> L = ld2(&uz[own - 2]), R = ld2(&uz[own + 2]);
+                const Pair<T> ym2 = ld2(&uz[own - 2 * kBX]), ym1 = ld2(&uz[own - kBX]);
+                const Pair<T> yp1 = ld2(&uz[own + kBX]), yp2 = ld2(&uz[own + 2 * kBX]);
+                T lap0 = qz[2].a - T(2) * u0.a + qz[0].a;
+                T lap1 = qz[2].b - T(2) * u0.b + qz[0].b;
+                lap0 += perp(c.a, code_shift(2, 0), L.a, L.b, u0.a, u0.b, R.a);
+                lap1 += perp(c.b, code_shift(2, 0), L.b, u0.a, u0.b, R.a, R.b);
+                lap0 += perp(c.a, code_shift(2, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
+                lap1 += perp(c.b, code_shift(2, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
+                if (B.alpha) {
+                    const int zp = nb_coord(m + 1, nz, B.per[2]);
+                    const long long g2 = (long long)(zp >= 0 ? zp : m) * plane + gin_own;
+                    lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0.a;
+                    lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[g2 + 1]) * u0.b;
                 }
+                T R0 = B.inv_re * lap0 - (pn_cur.a - pn_prev.a) + fz;
+                T R1 = B.inv_re * lap1 - (pn_cur.b - pn_prev.b) + fz;
+                if (SRC) {
+                    const Pair<T> sz = ld2(P.src + 2 * N + gidx);
+                    R0 += sz.a;
+                    R1 += sz.b;
+                }
+                uz_n.a = (c.a & node_bit(2)) ? u0.a + B.dt * R0 : u0.a;
+                uz_n.b = (c.b & node_bit(2)) ? u0.b + B.dt * R1 : u0.b;
             }
         }
-        P.uout[gidx] = un[0];
-        P.uout[N + gidx] = un[1];
-        P.uout[2 * N + gidx] = un[2];
-        P.pout[gidx] = pn_prev;
+        *reinterpret_cast<Pair<T> *>(outx) = ux_n;
+        *reinterpret_cast<Pair<T> *>(outx + N) = uy_n;
+        *reinterpret_cast<Pair<T> *>(outx + 2 * N) = uz_n;
+        *reinterpret_cast<Pair<T> *>(outp) = pn_prev;
+        outx += plane;
+        outp += plane;
         if (REDUCE) {
-            acc[0] += (double)un[0];
-            acc[1] += (double)un[1];
-            acc[2] += (double)un[2];
+            acc[0] += (double)ux_n.a + (double)ux_n.b;
+            acc[1] += (double)uy_n.a + (double)uy_n.b;
+            acc[2] += (double)uz_n.a + (double)uz_n.b;
         }
     }
     cp_async_wait<0>();
@@ -375,15 +471,14 @@ __global__ void __launch_bounds__(kNT, 3)
         for (int k = 0; k < 4; ++k)
             for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
         __shared__ double red[kNT / 32][4];
-        const int warp = tid >> 5, lane = tid & 31;
         if (lane == 0)
-            for (int k = 0; k < 4; ++k) red[warp][k] = acc[k];
+            for (int k = 0; k < 4; ++k) red[ty][k] = acc[k];
         __syncthreads();
         if (tid < 4) {
-            double s = 0.0;
-            for (int w = 0; w < kNT / 32; ++w) s += red[w][tid];
+            double sum = 0.0;
+            for (int w = 0; w < kNT / 32; ++w) sum += red[w][tid];
             const long long blk = (long long)tile * gridDim.y + blockIdx.y;
-            P.partials[blk * 4 + tid] = s;
+            P.partials[blk * 4 + tid] = sum;
         }
     }
 }
@@ -393,13 +488,14 @@ struct TiledShape {
     int tiles_x, tiles_y, zchunk, nzc;
 };
 
-inline TiledShape tiled_shape(int nx, int ny, int nz) {
+inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1) {
     TiledShape s;
     s.tiles_x = (nx + kTX - 1) / kTX;
     s.tiles_y = (ny + kTY - 1) / kTY;
-    // z chunks: long enough to amortise the 4-plane start-up, enough CTAs to fill the GPU
-    int zc = 64;
-    while (zc > 8 && (long long)s.tiles_x * s.tiles_y * ((nz + zc - 1) / zc) < 152 * 6) zc /= 2;
+    // z chunks: long enough to amortise the 4-plane start-up, enough CTAs (all drives) for
+    // about four waves of 2 CTAs on each of the 152 SMs
+    int zc = 128;
+    while (zc > 8 && (long long)s.tiles_x * s.tiles_y * nprob * ((nz + zc - 1) / zc) < 152 * 2 * 4) zc /= 2;
     s.zchunk = zc < nz ? zc : nz;
     s.nzc = (nz + s.zchunk - 1) / s.zchunk;
     return s;
@@ -414,19 +510,21 @@ inline bool tiled_supported(int nx, int ny, int nz, int nprob) {
 }
 
 template <typename T>
-inline long long tiled_num_blocks(int nx, int ny, int nz) {
-    TiledShape s = tiled_shape(nx, ny, nz);
+inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob) {
+    TiledShape s = tiled_shape(nx, ny, nz, nprob);
     return (long long)s.tiles_x * s.tiles_y * s.nzc;
 }
 
 template <typename T, int MODE, bool RED, bool SRC>
 inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, cudaStream_t s) {
-    const TiledShape sh = tiled_shape(B.nx, B.ny, B.nz);
+    const TiledShape sh = tiled_shape(B.nx, B.ny, B.nz, B.nprob);
     const size_t smem = sizeof(TiledSmem<T>);
     auto kern = sweep_tiled_kernel<T, MODE, RED, SRC>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
