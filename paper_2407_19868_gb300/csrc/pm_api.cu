@@ -383,13 +383,16 @@ struct Solver {
 
 struct Monitor {
     double q_prev[3] = {0, 0, 0};
-    double d_prev = -1.0;
+    double d_prev = -1.0, d_best = INFINITY;
     double delta = INFINITY, err = INFINITY;
+    int stalled = 0;  // consecutive windows without a new smallest change
     bool converged = false;
     // Window criterion (reading of Sec. 7.1, eps = delta|q| / |q|): relative change of
-    // the mean velocity over one window, and its geometric-tail extrapolation.
-    void update(const double q[3], int dir, double tol) {
-        double ref = std::fabs(q[dir]);
+    // the mean velocity over one window, and its geometric-tail extrapolation.  ref > 0
+    // replaces |q_dir| as the denominator (defect correction: the correction's mean is
+    // measured against the full solution's).
+    void update(const double q[3], int dir, double tol, double ref_in = 0.0) {
+        const double ref = ref_in > 0 ? ref_in : std::fabs(q[dir]);
         double ch = 0.0;
         for (int d = 0; d < 3; ++d) ch = std::fmax(ch, std::fabs(q[d] - q_prev[d]));
         delta = ref > 0 ? ch / ref : INFINITY;
@@ -401,15 +404,33 @@ struct Monitor {
         } else
             err = INFINITY;
         d_prev = delta;
+        if (delta < 0.9 * d_best) {
+            d_best = delta;
+            stalled = 0;
+        } else
+            ++stalled;
         for (int d = 0; d < 3; ++d) q_prev[d] = q[d];
         converged = delta < tol && err < tol;
     }
 };
 
+// Criterion of one run: tolerance, optional fixed reference scale per drive, and whether
+// a stall (no new smallest change for 6 windows) ends the run (FP32 floor).
+struct RunCriterion {
+    double tol = 0.0;
+    double ref[kMaxBatch] = {0, 0, 0, 0};
+    bool stop_on_stall = false;
+    long long max_iter = 0;
+};
+
 // Runs the batch to convergence from the loaded state.  Returns a pm_status.
 template <typename T>
-int run_to_convergence(Solver<T> &S, pm_stats *st, double t0) {
+int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion *crit = nullptr) {
     const pm_options &o = S.o;
+    RunCriterion defc;
+    defc.tol = o.tol;
+    defc.max_iter = o.max_iter;
+    const RunCriterion &C = crit ? *crit : defc;
     int M = o.check_every + (o.check_every & 1);
     Monitor mon[kMaxBatch];
     int status = PM_OK;
@@ -474,8 +495,8 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0) {
             const double *q = S.hq + 4 * k;
             if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) || !std::isfinite(q[3]))
                 bad = true;
-            mon[k].update(q, S.dir[k], o.tol);
-            all = all && mon[k].converged;
+            mon[k].update(q, S.dir[k], C.tol, C.ref[k]);
+            all = all && (mon[k].converged || (C.stop_on_stall && mon[k].stalled >= 6));
             if (st) {
                 st[k].div_res = std::sqrt(q[3]);
                 for (int d = 0; d < 3; ++d) st[k].q[d] = q[d];
@@ -486,7 +507,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0) {
             break;
         }
         if (all) break;
-        if (iters >= o.max_iter) {
+        if (iters >= C.max_iter) {
             status = PM_ERR_NOT_CONVERGED;
             break;
         }
@@ -516,6 +537,105 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0) {
             st[k].seconds = now_s() - t0;
             st[k].status = status;
         }
+    return status;
+}
+
+// Defect correction (precision pattern, not in the paper): FP32 sweeps to their floor,
+// then rounds of  r = b - K x64 (FP64 residual)  ->  K d = r by FP32 sweeps from d = 0
+// ->  x64 += d  until a round moves the mean velocity by less than tol.  The FP32 sweeps
+// only ever carry a correction, so their rounding is relative to the correction.
+// On return u64 / p64 hold the FP64 state of every drive and st[k].q its mean velocity.
+int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double t0, double **u64, double **p64) {
+    const pm_options &o = S.o;
+    const long long N = g.N;
+    RunCriterion c1;
+    c1.tol = o.dc_switch_tol > o.tol ? o.dc_switch_tol : o.tol;
+    c1.max_iter = o.max_iter;
+    c1.stop_on_stall = true;
+    int status = run_to_convergence<float>(S, st, t0, &c1);
+    if (status != PM_OK && status != PM_ERR_NOT_CONVERGED) return status;
+    long long iters = st[0].iters, timed = st[0].sweeps_timed;
+    double ms = st[0].sweep_ms * (double)st[0].sweeps_timed;
+    float *r32[kMaxBatch] = {nullptr, nullptr, nullptr, nullptr};
+    double q64[kMaxBatch][3];
+    int rc;
+    const int nb = 152 * 4;
+    double *part = nullptr;
+    if ((rc = S.scr.alloc(&part, (size_t)S.nprob * nb * 4))) return rc;
+    for (int k = 0; k < S.nprob; ++k) {
+        if ((rc = S.scr.alloc(&u64[k], 3 * (size_t)N)) || (rc = S.scr.alloc(&p64[k], (size_t)N)) ||
+            (rc = S.scr.alloc(&r32[k], 4 * (size_t)N)))
+            return rc;
+        scale_copy_kernel<double, float><<<launch_grid(3 * N), 256, 0, S.s>>>(u64[k], S.F[k].u[S.F[k].cur], 1.0, 3 * N);
+        scale_copy_kernel<double, float><<<launch_grid(N), 256, 0, S.s>>>(p64[k], S.F[k].p[S.F[k].cur], 1.0, N);
+        for (int d = 0; d < 3; ++d) q64[k][d] = st[k].q[d];
+    }
+    PM_CK(cudaGetLastError());
+    int rounds = 0;
+    pm_stats rs[kMaxBatch];
+    for (rounds = 1; rounds <= o.dc_max_rounds; ++rounds) {
+        RunCriterion c2;
+        c2.tol = o.tol;
+        c2.max_iter = o.max_iter;
+        c2.stop_on_stall = true;
+        for (int k = 0; k < S.nprob; ++k) {
+            double f[3] = {0, 0, 0};
+            f[S.dir[k]] = S.force[k];
+            residual64_kernel<<<launch_grid(N), 256, 0, S.s>>>(g.flags, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
+                                                               u64[k], p64[k], 1.0 / o.Re, f[0], f[1], f[2], r32[k]);
+            for (int b = 0; b < 2; ++b) {
+                PM_CK(cudaMemsetAsync(S.F[k].u[b], 0, sizeof(float) * 3 * N, S.s));
+                PM_CK(cudaMemsetAsync(S.F[k].p[b], 0, sizeof(float) * N, S.s));
+            }
+            S.F[k].cur = 0;
+            S.src[k] = r32[k];
+            c2.ref[k] = std::fabs(q64[k][S.dir[k]]);
+        }
+        PM_CK(cudaGetLastError());
+        std::memset(rs, 0, sizeof(rs));
+        status = run_to_convergence<float>(S, rs, t0, &c2);
+        if (status != PM_OK && status != PM_ERR_NOT_CONVERGED) break;
+        iters += rs[0].iters;
+        timed += rs[0].sweeps_timed;
+        ms += rs[0].sweep_ms * (double)rs[0].sweeps_timed;
+        double moved = 0.0;
+        for (int k = 0; k < S.nprob; ++k) {
+            accumulate_kernel<<<nb, 256, 0, S.s>>>(u64[k], p64[k], S.F[k].u[S.F[k].cur], S.F[k].p[S.F[k].cur], N,
+                                                  part + (size_t)k * nb * 4);
+        }
+        reduce_partials_kernel<<<S.nprob, 256, 0, S.s>>>(part, nb, N, S.dq);
+        PM_CK(cudaGetLastError());
+        PM_CK(cudaMemcpyAsync(S.hq, S.dq, sizeof(double) * S.nprob * 4, cudaMemcpyDeviceToHost, S.s));
+        PM_CK(cudaStreamSynchronize(S.s));
+        for (int k = 0; k < S.nprob; ++k) {
+            const double ref = std::fabs(S.hq[4 * k + S.dir[k]]);
+            for (int d = 0; d < 3; ++d) {
+                const double qn = S.hq[4 * k + d];
+                if (!std::isfinite(qn)) status = PM_ERR_DIVERGED;
+                moved = std::fmax(moved, ref > 0 ? std::fabs(qn - q64[k][d]) / ref : INFINITY);
+                q64[k][d] = qn;
+            }
+            st[k].delta = rs[k].delta;
+            st[k].err_est = rs[k].err_est;
+            st[k].div_res = rs[k].div_res;
+        }
+        if (status == PM_ERR_DIVERGED) break;
+        if (moved < o.tol) {
+            status = PM_OK;
+            break;
+        }
+        status = PM_ERR_NOT_CONVERGED;
+    }
+    for (int k = 0; k < S.nprob; ++k) {
+        S.src[k] = nullptr;
+        for (int d = 0; d < 3; ++d) st[k].q[d] = q64[k][d];
+        st[k].iters = iters;
+        st[k].sweeps_timed = timed;
+        st[k].sweep_ms = timed ? ms / (double)timed : 0.0;
+        st[k].dc_rounds = rounds > o.dc_max_rounds ? o.dc_max_rounds : rounds;
+        st[k].seconds = now_s() - t0;
+        st[k].status = status;
+    }
     return status;
 }
 
@@ -553,6 +673,13 @@ int solve_batch(const Geometry &g, const pm_options *o, cudaStream_t s, Scratch 
         S.force[k] = 1.0;  // Sec. 4: grad p = 1 per voxel in iteration units
     }
     return run_to_convergence<T>(S, st, t0);
+}
+
+inline int dc_dispatch(Solver<float> &S, const Geometry &g, pm_stats *st, double t0, double **u64, double **p64) {
+    return defect_correction(S, g, st, t0, u64, p64);
+}
+inline int dc_dispatch(Solver<double> &, const Geometry &, pm_stats *, double, double **, double **) {
+    return PM_ERR_UNSUPPORTED;
 }
 
 int count_fluid(const std::vector<uint8_t> &m) {
@@ -615,14 +742,28 @@ int tensor_like(const pm_domain *dom, const pm_options *o, int ndirs, const int 
                 sanitize_kernel<T><<<launch_grid(g.N), 256, 0, ss.s>>>(g.flags, g.N, ut, pt);
                 if (cudaGetLastError() != cudaSuccess) return PM_ERR_CUDA;
             }
-            status = run_to_convergence<T>(S, bst, t0);
+            double *u64[kMaxBatch] = {nullptr, nullptr, nullptr, nullptr};
+            double *p64[kMaxBatch] = {nullptr, nullptr, nullptr, nullptr};
+            if (o->precision == PM_FP32_DC64)
+                status = dc_dispatch(S, g, bst, t0, u64, p64);
+            else
+                status = run_to_convergence<T>(S, bst, t0);
             if (status == PM_OK || status == PM_ERR_NOT_CONVERGED) {
-                if (u_out)
-                    scale_copy_kernel<float, T><<<launch_grid(3 * g.N), 256, 0, ss.s>>>(u_out, S.F[0].u[S.F[0].cur],
-                                                                                       uscale, 3 * g.N);
-                if (p_out)
-                    scale_copy_kernel<float, T><<<launch_grid(g.N), 256, 0, ss.s>>>(p_out, S.F[0].p[S.F[0].cur],
-                                                                                   pscale, g.N);
+                if (u_out) {
+                    if (u64[0])
+                        scale_copy_kernel<float, double><<<launch_grid(3 * g.N), 256, 0, ss.s>>>(u_out, u64[0], uscale,
+                                                                                                3 * g.N);
+                    else
+                        scale_copy_kernel<float, T><<<launch_grid(3 * g.N), 256, 0, ss.s>>>(
+                            u_out, S.F[0].u[S.F[0].cur], uscale, 3 * g.N);
+                }
+                if (p_out) {
+                    if (p64[0])
+                        scale_copy_kernel<float, double><<<launch_grid(g.N), 256, 0, ss.s>>>(p_out, p64[0], pscale, g.N);
+                    else
+                        scale_copy_kernel<float, T><<<launch_grid(g.N), 256, 0, ss.s>>>(p_out, S.F[0].p[S.F[0].cur],
+                                                                                       pscale, g.N);
+                }
                 if (cudaGetLastError() != cudaSuccess) status = PM_ERR_CUDA;
             }
         }
@@ -838,7 +979,6 @@ int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_opt
     if (rc) return rc;
     if ((rc = validate_options(o))) return rc;
     if (dir < 0 || dir > 2 || !(drive > 0)) return PM_ERR_INVALID_ARG;
-    if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
     double kc[3][3];
     pm_stats local;
     int dirs[1] = {dir};
@@ -857,7 +997,6 @@ int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_options 
     if (rc) return rc;
     if ((rc = validate_options(o))) return rc;
     if (!k_out || !(drive > 0)) return PM_ERR_INVALID_ARG;
-    if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
     double kc[3][3];
     int dirs[3] = {0, 1, 2};
     if (o->precision == PM_FP64)

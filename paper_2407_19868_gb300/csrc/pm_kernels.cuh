@@ -186,6 +186,96 @@ __global__ void __launch_bounds__(256) sweep_simple_kernel(const SweepBatch<T> B
     }
 }
 
+// ------------------------------------------------------------------ defect correction
+// Steady residual of the discrete Stokes system in FP64 (Sec. 3, 4), for the defect
+// correction of FP32 sweeps:
+//   r_u(d, c) = (1/Re) [A_d u + sum_{i != d} S_i u](c) - (p(c+e_d) - p(c)) + f_d  (fluid nodes)
+//   r_p(c)    = -(D u)(c)                                                      (pore cells)
+// stored as FP32: the correction only needs r to a few digits relative to itself.
+__global__ void residual64_kernel(const uint8_t *__restrict__ fl, int nx, int ny, int nz, int px, int py,
+                                  int pz, const double *__restrict__ u, const double *__restrict__ p,
+                                  double inv_re, double f0, double f1, double f2, float *__restrict__ r) {
+    const long long N = (long long)nx * ny * nz;
+    const double f[3] = {f0, f1, f2};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx);
+        const long long rr = c / nx;
+        const int y = (int)(rr % ny), z = (int)(rr / ny);
+        auto lin = [&](int xx, int yy, int zz) -> long long {
+            return (long long)xx + (long long)nx * ((long long)yy + (long long)ny * zz);
+        };
+        auto U = [&](int d, int xx, int yy, int zz) -> double {
+            return (xx < 0 || yy < 0 || zz < 0) ? 0.0 : u[d * N + lin(xx, yy, zz)];
+        };
+        auto F = [&](int d, int xx, int yy, int zz) -> bool {
+            return !(xx < 0 || yy < 0 || zz < 0) && (fl[lin(xx, yy, zz)] & node_bit(d));
+        };
+        const int xm1 = nb_coord(x - 1, nx, px), xp1 = nb_coord(x + 1, nx, px);
+        const int xm2 = nb_coord(x - 2, nx, px), xp2 = nb_coord(x + 2, nx, px);
+        const int ym1 = nb_coord(y - 1, ny, py), yp1 = nb_coord(y + 1, ny, py);
+        const int ym2 = nb_coord(y - 2, ny, py), yp2 = nb_coord(y + 2, ny, py);
+        const int zm1 = nb_coord(z - 1, nz, pz), zp1 = nb_coord(z + 1, nz, pz);
+        const int zm2 = nb_coord(z - 2, nz, pz), zp2 = nb_coord(z + 2, nz, pz);
+        const uint8_t f0c = fl[c];
+        for (int d = 0; d < 3; ++d) {
+            double R = 0.0;
+            if (f0c & node_bit(d)) {
+                const double u0 = u[d * N + c];
+                double lap;
+                if (d == 0) lap = U(0, xp1, y, z) - 2.0 * u0 + U(0, xm1, y, z);
+                else if (d == 1) lap = U(1, x, yp1, z) - 2.0 * u0 + U(1, x, ym1, z);
+                else lap = U(2, x, y, zp1) - 2.0 * u0 + U(2, x, y, zm1);
+                if (d != 0)
+                    lap += perp_d2(u0, U(d, xm2, y, z), U(d, xm1, y, z), U(d, xp1, y, z), U(d, xp2, y, z),
+                                   F(d, xm2, y, z), F(d, xm1, y, z), F(d, xp1, y, z), F(d, xp2, y, z));
+                if (d != 1)
+                    lap += perp_d2(u0, U(d, x, ym2, z), U(d, x, ym1, z), U(d, x, yp1, z), U(d, x, yp2, z),
+                                   F(d, x, ym2, z), F(d, x, ym1, z), F(d, x, yp1, z), F(d, x, yp2, z));
+                if (d != 2)
+                    lap += perp_d2(u0, U(d, x, y, zm2), U(d, x, y, zm1), U(d, x, y, zp1), U(d, x, y, zp2),
+                                   F(d, x, y, zm2), F(d, x, y, zm1), F(d, x, y, zp1), F(d, x, y, zp2));
+                const long long ce = lin(d == 0 ? xp1 : x, d == 1 ? yp1 : y, d == 2 ? zp1 : z);
+                R = inv_re * lap - (p[ce] - p[c]) + f[d];
+            }
+            r[d * N + c] = (float)R;
+        }
+        double rp = 0.0;
+        if (f0c & kFlagCell)
+            rp = -((u[c] - U(0, xm1, y, z)) + (u[N + c] - U(1, x, ym1, z)) + (u[2 * N + c] - U(2, x, y, zm1)));
+        r[3 * N + c] = (float)rp;
+    }
+}
+
+// x64 += d32 over the 4N values of one state, and FP64 block sums of the new u
+// (partials[blk][0..2]; [3] = 0) for the mean velocity.
+__global__ void accumulate_kernel(double *__restrict__ u64, double *__restrict__ p64, const float *__restrict__ du,
+                                  const float *__restrict__ dp, long long N, double *__restrict__ partials) {
+    double a[3] = {0.0, 0.0, 0.0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        for (int d = 0; d < 3; ++d) {
+            const double v = u64[d * N + c] + (double)du[d * N + c];
+            u64[d * N + c] = v;
+            a[d] += v;
+        }
+        p64[c] += (double)dp[c];
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    __shared__ double red[8][3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) red[warp][k] = a[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        if (threadIdx.x < 3)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
 // Sums the block partials of each problem in a fixed order (deterministic) and scales
 // by 1/N: out[prob][0..2] = q_d, out[prob][3] = |D u|^2.
 __global__ void reduce_partials_kernel(const double *partials, long long nblk, long long N,

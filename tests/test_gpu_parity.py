@@ -180,3 +180,45 @@ def test_config2_full_size_batched_launch(api, oracle_mod):
     scale = np.abs(np.diag(K)).max()
     np.testing.assert_allclose(r["k_raw"], K, rtol=0, atol=1e-5 * scale)
     np.testing.assert_allclose(np.diag(r["k_raw"]), np.diag(K), rtol=1e-5)
+
+
+def test_defect_correction_config1(api, config1, config1_oracle):
+    """FP32 sweeps + FP64 defect correction reach the oracle's converged k far below the
+    FP32 floor: 1e-8 relative on k_xx, off-diagonals within 1e-8 of k_xx."""
+    r = api.solve_direction(config1, 0, tol=1e-11, precision="fp32_dc64", check_every=100)
+    assert r["status"] == api.PM_OK
+    assert r["stats"]["dc_rounds"] >= 1
+    k, ko = r["k_col"], config1_oracle
+    assert k[0] == pytest.approx(ko[0], rel=1e-8)
+    np.testing.assert_allclose(k[1:], ko[1:], rtol=0, atol=1e-8 * abs(ko[0]))
+
+
+def test_defect_correction_full_tensor(api, oracle_mod):
+    mask = G.overlapping_spheres((20, 24, 28), 3.0, 0.6, seed=12)
+    _, k_raw_o, _ = oracle_mod.ktensor(mask, tol=1e-12)
+    r = api.permeability_tensor(mask, tol=1e-11, precision="fp32_dc64")
+    assert r["status"] == api.PM_OK
+    scale = np.abs(np.diag(k_raw_o)).max()
+    np.testing.assert_allclose(r["k_raw"], k_raw_o, rtol=0, atol=1e-8 * scale)
+
+
+@pytest.mark.slow
+def test_config2_ktensor_against_oracle_reference(api):
+    """256^3 benchmark geometry, full tensor in the benchmark's launch configuration with
+    defect correction, against the oracle's converged columns stored by
+    tests/golden/make_reference.py (the mask hash must match): 1e-5 relative on every
+    component, off-diagonals included."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "reference_k.json")))
+    if "config2" not in ref:
+        pytest.skip("oracle reference for the 256^3 geometry not generated yet")
+    ref = ref["config2"]
+    mask, _ = G.rsa_sphere_pack((256, 256, 256), 10.0, 0.3, 4.0, 25.0, 0.38, seed=2)
+    assert G.mask_sha256(mask) == ref["sha256"]
+    r = api.permeability_tensor(torch.from_numpy(mask).cuda(), tol=1e-8, precision="fp32_dc64")
+    assert r["status"] == api.PM_OK
+    for j, col in ref["columns"].items():
+        ko = np.array(col["k_col"])
+        kg = r["k_raw"][:, int(j)]
+        np.testing.assert_allclose(kg, ko, rtol=1e-5, atol=0)
