@@ -573,6 +573,9 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
     PM_CK(cudaGetLastError());
     int rounds = 0;
     pm_stats rs[kMaxBatch];
+    // the residual carries the drive; the correction solves K d = r have no body force
+    double force[kMaxBatch];
+    for (int k = 0; k < S.nprob; ++k) force[k] = S.force[k];
     for (rounds = 1; rounds <= o.dc_max_rounds; ++rounds) {
         RunCriterion c2;
         c2.tol = o.tol;
@@ -580,7 +583,8 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
         c2.stop_on_stall = true;
         for (int k = 0; k < S.nprob; ++k) {
             double f[3] = {0, 0, 0};
-            f[S.dir[k]] = S.force[k];
+            f[S.dir[k]] = force[k];
+            S.force[k] = 0.0;
             residual64_kernel<<<launch_grid(N), 256, 0, S.s>>>(g.flags, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
                                                                u64[k], p64[k], 1.0 / o.Re, f[0], f[1], f[2], r32[k]);
             for (int b = 0; b < 2; ++b) {
@@ -628,6 +632,7 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
     }
     for (int k = 0; k < S.nprob; ++k) {
         S.src[k] = nullptr;
+        S.force[k] = force[k];
         for (int d = 0; d < 3; ++d) st[k].q[d] = q64[k][d];
         st[k].iters = iters;
         st[k].sweeps_timed = timed;
