@@ -183,6 +183,24 @@ PM_API int pm_solve_direction(const pm_domain *dom, int dir, double drive, const
 PM_API int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_options *opt,
                            double k_out[9], double k_raw[9], pm_stats st[3], void *cuda_stream);
 
+/* Adjoint sensitivity of J = sum_ij w_ij k_ij to a per-cell drag field alpha (not in the
+ * paper: the steady momentum equation of Sec. 3 / 4 gains -(1/Re) alpha_f u with the face
+ * value alpha_f = (alpha(c) + alpha(c+e_d)) / 2, alpha in units of mu / dx^2; alpha = 0 is
+ * the paper's problem).  Forward solves for every drive j with a nonzero column of w,
+ * solves of the transposed system (viscous operator transposed) for every row i, then
+ *   dJ/d alpha_c = -(dx^2 / (2 Re^2 N)) sum_ij w_ij sum_{faces F of c} v^(i)_F u^(j)_F
+ * (u^(j), v^(i) in iteration units for a unit drive).
+ *   alpha: device, N floats, or NULL for 0.      w: host, 9 doubles, row-major.
+ *   dJ_dalpha: device, N floats, caller-owned, written for every cell (dx^2 units of k);
+ *   NULL: forward only -- the three drives are solved with alpha and k_raw is returned
+ *   (w may then be NULL).
+ *   J (host, may be NULL): the objective.  k_raw (host, 9 or NULL): the forward columns.
+ *   Precision PM_FP32_RED64 or PM_FP64 (PM_FP32_DC64: PM_ERR_UNSUPPORTED).
+ *   Errors: PM_ERR_INVALID_ARG (w all zero), PM_ERR_NO_FLUID, PM_ERR_NOT_CONVERGED,
+ *   PM_ERR_DIVERGED, PM_ERR_OOM, PM_ERR_CUDA. */
+PM_API int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *opt,
+                          float *dJ_dalpha, double *J, double k_raw[9], void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -255,3 +255,46 @@ def ktensor(mask, dirs=(0, 1, 2), bc=(PERIODIC, PERIODIC, PERIODIC), tol=1e-10, 
         runs[j] = r
     k_raw = permeability_from_q(Q, dx=dx)
     return symmetrise(k_raw), k_raw, runs
+
+
+def sensitivity(mask, w, alpha=None, bc=(PERIODIC, PERIODIC, PERIODIC), tol=1e-12, check_every=100,
+                dom: Domain | None = None):
+    """dJ/d alpha for J = sum_ij w_ij k_ij with a per-cell drag alpha in the momentum
+    equation ((1/Re)(L u - alpha_f u), alpha_f = face average; alpha = 0 is the paper).
+
+    Adjoint of the steady system (not in the paper, derived from it): with u^(j) the
+    forward solution for drive j and v^(i) the solution of the transposed problem
+    (viscous operator L^T) for a unit drive along i,
+        dk_ij / d alpha_c = -(1 / (2 Re^2 N)) sum over the six faces F of cell c of v^(i)_F u^(j)_F
+    (iteration units, unit drive).  Returns (dJ [nz, ny, nx], J, k_raw)."""
+    w = np.asarray(w, dtype=np.float64).reshape(3, 3)
+    dom = dom or Domain(mask, bc)
+    nz, ny, nx = dom.shape
+    fwd, adj = {}, {}
+    k = np.zeros((3, 3))
+    for j in range(3):
+        if np.any(w[:, j] != 0):
+            r = dom.solve(j, tol=tol, check_every=check_every, alpha=alpha)
+            fwd[j] = r["U"]
+            k[:, j] = r["q"] / RE_PAPER
+    for i in range(3):
+        if np.any(w[i, :] != 0):
+            adj[i] = dom.solve(i, tol=tol, check_every=check_every, alpha=alpha, transposed=True)["U"]
+    per = [b == PERIODIC for b in bc]
+    s = np.zeros(dom.shape)
+    for i, V in adj.items():
+        for j, U in fwd.items():
+            if w[i, j] == 0:
+                continue
+            for d in range(3):
+                prod = V[d] * U[d]  # on the +d face of every cell
+                axis = 2 - d        # array axis of direction d ([z][y][x])
+                lower = np.roll(prod, 1, axis=axis)  # the -d face of each cell
+                if not per[d]:
+                    idx = [slice(None)] * 3
+                    idx[axis] = 0
+                    lower[tuple(idx)] = 0.0
+                s += w[i, j] * (prod + lower)
+    N = dom.N
+    dJ = -s / (2.0 * RE_PAPER * RE_PAPER * N)
+    return dJ, float(np.sum(w * k)), k

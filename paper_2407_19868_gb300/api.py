@@ -37,7 +37,7 @@ _PRECISION = {"fp32": FP32_RED64, "fp32_red64": FP32_RED64, "fp32_dc64": FP32_DC
 
 # every function the header declares (checked by the ABI test)
 EXPORTED = ["pm_default_options", "pm_strerror", "pm_version", "pm_time_step", "pm_iterate",
-            "pm_iterate_noalloc", "pm_solve_direction", "pm_permeability_tensor"]
+            "pm_iterate_noalloc", "pm_solve_direction", "pm_permeability_tensor", "pm_sensitivity"]
 
 
 class PMError(RuntimeError):
@@ -107,6 +107,7 @@ def load():
                                          vp, vp, vp, vp, dp, C.POINTER(Stats), vp]
         L.pm_permeability_tensor.argtypes = [C.POINTER(Domain), C.c_double, C.POINTER(Options), dp, dp,
                                              C.POINTER(Stats), vp]
+        L.pm_sensitivity.argtypes = [C.POINTER(Domain), vp, dp, C.POINTER(Options), vp, dp, dp, vp]
         _LIB = L
         return L
 
@@ -224,3 +225,58 @@ def permeability_tensor(mask, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts
     _check(st, "pm_permeability_tensor", soft=(PM_OK, PM_ERR_NOT_PERCOLATING, PM_ERR_NOT_CONVERGED))
     return {"k": np.array(k[:]).reshape(3, 3), "k_raw": np.array(kr[:]).reshape(3, 3),
             "stats": [s[i].as_dict() for i in range(3)], "status": st}
+
+
+def sensitivity(mask, w=None, alpha=None, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts):
+    """Adjoint sensitivity of J = sum w_ij k_ij to a per-cell drag alpha (pm_sensitivity).
+    alpha: CUDA float32 tensor (nz, ny, nx) or None.  With w=None only the forward solves
+    run and dJ is None.  Returns dict(dJ, J, k_raw, status)."""
+    import torch
+    m = _Mask(mask, dx=dx, bc=bc)
+    o = options(**opts)
+    a = None
+    if alpha is not None:
+        a = alpha.detach().to(device="cuda", dtype=torch.float32).contiguous()
+        if a.numel() != m.N:
+            raise ValueError("alpha must have one value per voxel")
+    dJ = torch.empty(m.shape, dtype=torch.float32, device="cuda") if w is not None else None
+    wa = (C.c_double * 9)(*np.asarray(w, dtype=np.float64).reshape(-1)) if w is not None else None
+    J = C.c_double(0.0)
+    kr = (C.c_double * 9)()
+    st = load().pm_sensitivity(C.byref(m.dom), a.data_ptr() if a is not None else None, wa, C.byref(o),
+                               dJ.data_ptr() if dJ is not None else None, C.byref(J), kr, _stream(stream))
+    _check(st, "pm_sensitivity", soft=(PM_OK, PM_ERR_NOT_CONVERGED))
+    return {"dJ": dJ, "J": float(J.value), "k_raw": np.array(kr[:]).reshape(3, 3), "status": st}
+
+
+def _ktensor_fn():
+    import torch
+
+    class KTensorFn(torch.autograd.Function):
+        """k_raw(alpha): the 3x3 permeability tensor of the mask with a per-cell drag
+        alpha (alpha = 0 is the paper's problem).  backward(grad_k) is one adjoint
+        solve: pm_sensitivity with w = grad_k gives d(sum grad_k * k)/d alpha."""
+
+        @staticmethod
+        def forward(ctx, alpha, mask, opts):
+            r = sensitivity(mask, None, alpha=alpha, **opts)
+            ctx.mask, ctx.opts = mask, opts
+            ctx.save_for_backward(alpha)
+            return torch.as_tensor(r["k_raw"], dtype=torch.float64, device=alpha.device)
+
+        @staticmethod
+        def backward(ctx, grad_k):
+            (alpha,) = ctx.saved_tensors
+            w = grad_k.detach().double().cpu().numpy()
+            if not np.any(w):
+                return torch.zeros_like(alpha), None, None
+            r = sensitivity(ctx.mask, w, alpha=alpha, **ctx.opts)
+            return r["dJ"].to(alpha.dtype), None, None
+
+    return KTensorFn
+
+
+def __getattr__(name):
+    if name == "KTensorFn":
+        return _ktensor_fn()
+    raise AttributeError(name)

@@ -254,6 +254,7 @@ struct Solver {
     long long nblk = 0;
     T dt = 0, dtc2 = 0, inv_re = 0;
     const T *alpha = nullptr;
+    bool transposed = false;  // adjoint solves: transpose of the viscous operator
 
     Solver(const Geometry &gg, const pm_options &oo, cudaStream_t ss, Scratch &sc)
         : g(gg), o(oo), s(ss), scr(sc) {}
@@ -311,6 +312,7 @@ struct Solver {
         for (int a = 0; a < 3; ++a) B.per[a] = g.per[a];
         B.N = g.N;
         B.flags = g.flags;
+        B.code = g.code;
         B.alpha = alpha;
         B.inv_re = inv_re;
         B.dt = dt;
@@ -331,10 +333,16 @@ struct Solver {
 
     template <int MODE, bool RED>
     void launch_simple(const SweepBatch<T> &B, bool has_src) {
-        if (has_src)
+        if (transposed)
+            sweep_simple_kernel<T, MODE, RED, false, true><<<grid(), block(), 0, s>>>(B);
+        else if (has_src)
             sweep_simple_kernel<T, MODE, RED, true><<<grid(), block(), 0, s>>>(B);
         else
             sweep_simple_kernel<T, MODE, RED, false><<<grid(), block(), 0, s>>>(B);
+    }
+
+    bool use_tiled() const {
+        return o.kernel == 0 && !transposed && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
     }
 
     // One sweep of the given mode; flips the ping-pong buffers.
@@ -342,8 +350,7 @@ struct Solver {
         SweepBatch<T> B = batch(reduce);
         bool has_src = false;
         for (int k = 0; k < nprob; ++k) has_src |= src[k] != nullptr;
-        const bool tiled = o.kernel == 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
-        if (tiled) {
+        if (use_tiled()) {
             int st = launch_tiled<T>(B, g.code, mode, reduce, has_src, s);
             if (st) return st;
         } else if (mode == kModeU) {
@@ -359,9 +366,7 @@ struct Solver {
     }
 
     long long reduce_blocks() const {
-        return (o.kernel == 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob))
-                   ? tiled_num_blocks<T>(g.nx, g.ny, g.nz, nprob)
-                   : nblk;
+        return use_tiled() ? tiled_num_blocks<T>(g.nx, g.ny, g.nz, nprob) : nblk;
     }
 
     int reduce_to_host_async() {
@@ -893,6 +898,88 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
     return PM_OK;
 }
 
+// Adjoint sensitivity (differentiation pattern, not in the paper).  J = sum w_ij k_ij with
+// a per-cell drag alpha; forward solves for the drives j with a nonzero column of w,
+// transposed solves for the rows i, then the face products (sensitivity_kernel).
+template <typename T>
+int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *o,
+                     float *dJ, double *J, double *k_raw, cudaStream_t s, Scratch &scr, double t0) {
+    Geometry g;
+    int rc = build_geometry(dom, s, scr, g);
+    if (rc) return rc;
+    const T *alpha_t = nullptr;
+    if (alpha) {
+        if (sizeof(T) == sizeof(float)) {
+            alpha_t = reinterpret_cast<const T *>(alpha);
+        } else {
+            T *a = nullptr;
+            if ((rc = scr.alloc(&a, (size_t)g.N))) return rc;
+            scale_copy_kernel<T, float><<<launch_grid(g.N), 256, 0, s>>>(a, alpha, 1.0, g.N);
+            PM_CK(cudaGetLastError());
+            alpha_t = a;
+        }
+    }
+    int fdirs[3], nf = 0, adirs[3], na = 0;
+    for (int j = 0; j < 3; ++j) {
+        bool col = !dJ, row = false;  // forward only: all three drives, no adjoint
+        for (int i = 0; i < 3 && dJ; ++i) {
+            col |= w[3 * i + j] != 0.0;
+            row |= w[3 * j + i] != 0.0;
+        }
+        if (col) fdirs[nf++] = j;
+        if (row) adirs[na++] = j;
+    }
+    if (nf == 0) return PM_ERR_INVALID_ARG;
+    Solver<T> F(g, *o, s, scr), A(g, *o, s, scr);
+    if ((rc = F.init(nf)) || (na > 0 && (rc = A.init(na)))) return rc;
+    F.alpha = alpha_t;
+    A.alpha = alpha_t;
+    A.transposed = true;
+    for (int k = 0; k < nf; ++k) {
+        F.dir[k] = fdirs[k];
+        F.force[k] = 1.0;
+    }
+    for (int k = 0; k < na; ++k) {
+        A.dir[k] = adirs[k];
+        A.force[k] = 1.0;
+    }
+    pm_stats sf[kMaxBatch], sa[kMaxBatch];
+    std::memset(sf, 0, sizeof(sf));
+    std::memset(sa, 0, sizeof(sa));
+    int st = run_to_convergence<T>(F, sf, t0);
+    if (st != PM_OK && st != PM_ERR_NOT_CONVERGED) return st;
+    if (na > 0) {
+        int st2 = run_to_convergence<T>(A, sa, t0);
+        if (st2 != PM_OK && st2 != PM_ERR_NOT_CONVERGED) return st2;
+        if (st == PM_OK) st = st2;
+    }
+    SensArgs<T> args{};
+    double kr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < nf; ++k) {
+        args.fwd[fdirs[k]] = F.F[k].u[F.F[k].cur];
+        for (int i = 0; i < 3; ++i) kr[3 * i + fdirs[k]] = sf[k].q[i] / o->Re * dom->voxel_size * dom->voxel_size;
+    }
+    for (int k = 0; k < na; ++k) args.adj[adirs[k]] = A.F[k].u[A.F[k].cur];
+    double Jv = 0.0;
+    for (int i = 0; i < 3 && w; ++i)
+        for (int j = 0; j < 3; ++j) {
+            args.w[i][j] = w[3 * i + j];
+            Jv += w[3 * i + j] * kr[3 * i + j];
+        }
+    // dk_ij/d alpha_c = -(1 / (2 Re^2 N)) sum_F v^(i)_F u^(j)_F  (unit drive), times dx^2
+    const double scale = -dom->voxel_size * dom->voxel_size / (2.0 * o->Re * o->Re * (double)g.N);
+    if (dJ) {
+        sensitivity_kernel<T><<<launch_grid(g.N), 256, 0, s>>>(args, g.nx, g.ny, g.nz, g.per[0], g.per[1],
+                                                              g.per[2], scale, dJ);
+        PM_CK(cudaGetLastError());
+    }
+    PM_CK(cudaStreamSynchronize(s));
+    if (J) *J = Jv;
+    if (k_raw)
+        for (int i = 0; i < 9; ++i) k_raw[i] = kr[i];
+    return st;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -993,6 +1080,31 @@ int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_opt
         rc = tensor_like<float>(dom, o, 1, dirs, drive, u, p, u0, p0, kc, st ? st : &local, cuda_stream);
     if (k_col)
         for (int i = 0; i < 3; ++i) k_col[i] = kc[0][i];
+    return rc;
+}
+
+int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *o,
+                   float *dJ_dalpha, double *J, double k_raw[9], void *cuda_stream) {
+    int rc = validate_domain(dom);
+    if (rc) return rc;
+    if ((rc = validate_options(o))) return rc;
+    if (dJ_dalpha && !w) return PM_ERR_INVALID_ARG;
+    if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
+    const double t0 = now_s();
+    std::vector<uint8_t> hm;
+    if ((rc = host_mask(dom, hm))) return rc;
+    if (!count_fluid(hm)) return PM_ERR_NO_FLUID;
+    StreamScope ss(cuda_stream);
+    if (ss.status) return ss.status;
+    {
+        Scratch scr(ss.s);
+        if (o->precision == PM_FP64)
+            rc = sensitivity_impl<double>(dom, alpha, w, o, dJ_dalpha, J, k_raw, ss.s, scr, t0);
+        else
+            rc = sensitivity_impl<float>(dom, alpha, w, o, dJ_dalpha, J, k_raw, ss.s, scr, t0);
+    }
+    cudaError_t e = cudaStreamSynchronize(ss.s);
+    if (rc == PM_OK && e != cudaSuccess) rc = map_cuda(e);
     return rc;
 }
 

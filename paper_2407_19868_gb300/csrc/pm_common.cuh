@@ -50,6 +50,7 @@ struct SweepBatch {
     int per[3];            // 1 = periodic axis, 0 = wall (outside counts as solid)
     long long N;
     const uint8_t *flags;  // N
+    const uint32_t *code;  // N stencil codes (wall cases), used by the transposed sweep
     const T *alpha;        // N per-cell drag or nullptr
     T inv_re, dt, dtc2;
     int nprob;

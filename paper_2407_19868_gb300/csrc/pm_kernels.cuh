@@ -6,6 +6,11 @@
 
 namespace pmgb {
 
+// Bit offset of the 3-bit wall code of node u_d across axis i in a stencil code word.
+__host__ __device__ constexpr int pmgb_code_shift(int d, int i) {
+    return d == 0 ? (i == 1 ? 4 : 7) : d == 1 ? (i == 0 ? 10 : 13) : (i == 0 ? 16 : 19);
+}
+
 // ------------------------------------------------------------------ neighbourhood
 // Algorithm 1 "Evaluate neighborhood": per cell the pore flag and the fluid flags of its
 // three +d face nodes (Sec. 4: a face between two pore cells carries flow; every face
@@ -65,11 +70,27 @@ __device__ __forceinline__ T perp_d2(T u0, T um2, T um1, T up1, T up2, bool Fm2,
     return Fm2 ? (T(2) * um1 - T(5) * u0 - c15 * um2) : (c83 * um1 - c163 * u0);
 }
 
+// Coefficients of the 3-bit wall code (kind, side) of the tiled kernel's stencil codes:
+// the second derivative across the flow of node b is
+//   A (u(b-1) + u(b+1)) + B u(b) + Cm u(b-2) + Cp u(b+2).
+template <typename T>
+__device__ __forceinline__ void wall_coef(uint32_t k3, T &A, T &Bc, T &Cm, T &Cp) {
+    const uint32_t kind = k3 & 3u;
+    A = kind == 0u ? T(1) : (kind == 2u ? T(2) : (kind == 3u ? T(8) / T(3) : T(0)));
+    Bc = kind == 0u ? T(-2) : (kind == 1u ? T(-8) : (kind == 2u ? T(-5) : T(-16) / T(3)));
+    const T c = kind == 2u ? T(-1) / T(5) : T(0);
+    Cm = (k3 & 4u) ? T(0) : c;
+    Cp = (k3 & 4u) ? c : T(0);
+}
+
 // ------------------------------------------------------------------ simple fused sweep
 // Reference implementation: one thread per cell, every operand loaded from global memory
 // (L1/L2 serve the neighbour reuse).  It defines the arithmetic the tiled kernel must
 // reproduce and serves small domains.
-template <typename T, int MODE, bool REDUCE, bool SRC>
+// TR: use the transpose of the viscous operator (adjoint solves).  Node a's transposed
+// term along axis i gathers, from each node b within two cells, b's own coefficient for
+// the offset that reaches a (read from b's stencil code).
+template <typename T, int MODE, bool REDUCE, bool SRC, bool TR = false>
 __global__ void __launch_bounds__(256) sweep_simple_kernel(const SweepBatch<T> B) {
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const long long N = B.N;
@@ -133,15 +154,58 @@ __global__ void __launch_bounds__(256) sweep_simple_kernel(const SweepBatch<T> B
                     if (d == 0) lap = U(0, xp1, y, z) - T(2) * u0 + U(0, xm1, y, z);
                     else if (d == 1) lap = U(1, x, yp1, z) - T(2) * u0 + U(1, x, ym1, z);
                     else lap = U(2, x, y, zp1) - T(2) * u0 + U(2, x, y, zm1);
-                    if (d != 0)
-                        lap += perp_d2(u0, U(d, xm2, y, z), U(d, xm1, y, z), U(d, xp1, y, z), U(d, xp2, y, z),
-                                       F(d, xm2, y, z), F(d, xm1, y, z), F(d, xp1, y, z), F(d, xp2, y, z));
-                    if (d != 1)
-                        lap += perp_d2(u0, U(d, x, ym2, z), U(d, x, ym1, z), U(d, x, yp1, z), U(d, x, yp2, z),
-                                       F(d, x, ym2, z), F(d, x, ym1, z), F(d, x, yp1, z), F(d, x, yp2, z));
-                    if (d != 2)
-                        lap += perp_d2(u0, U(d, x, y, zm2), U(d, x, y, zm1), U(d, x, y, zp1), U(d, x, y, zp2),
-                                       F(d, x, y, zm2), F(d, x, y, zm1), F(d, x, y, zp1), F(d, x, y, zp2));
+                    if (!TR) {
+                        if (d != 0)
+                            lap += perp_d2(u0, U(d, xm2, y, z), U(d, xm1, y, z), U(d, xp1, y, z), U(d, xp2, y, z),
+                                           F(d, xm2, y, z), F(d, xm1, y, z), F(d, xp1, y, z), F(d, xp2, y, z));
+                        if (d != 1)
+                            lap += perp_d2(u0, U(d, x, ym2, z), U(d, x, ym1, z), U(d, x, yp1, z), U(d, x, yp2, z),
+                                           F(d, x, ym2, z), F(d, x, ym1, z), F(d, x, yp1, z), F(d, x, yp2, z));
+                        if (d != 2)
+                            lap += perp_d2(u0, U(d, x, y, zm2), U(d, x, y, zm1), U(d, x, y, zp1), U(d, x, y, zp2),
+                                           F(d, x, y, zm2), F(d, x, y, zm1), F(d, x, y, zp1), F(d, x, y, zp2));
+                    } else {
+                        // transpose: sum over b = a + m e_i of b's coefficient for offset -m
+                        auto trans = [&](int i, const int cm2[3], const int cm1[3], const int cp1[3],
+                                         const int cp2[3]) -> T {
+                            const int sh = pmgb_code_shift(d, i);
+                            auto k3 = [&](const int q[3]) -> uint32_t {
+                                return (B.code[lin(q[0], q[1], q[2])] >> sh) & 7u;
+                            };
+                            T A, Bc, Cm, Cp, acc;
+                            wall_coef<T>((B.code[c] >> sh) & 7u, A, Bc, Cm, Cp);
+                            acc = Bc * u0;
+                            if (cm1[0] >= 0 && cm1[1] >= 0 && cm1[2] >= 0) {
+                                wall_coef<T>(k3(cm1), A, Bc, Cm, Cp);
+                                acc += A * U(d, cm1[0], cm1[1], cm1[2]);
+                            }
+                            if (cp1[0] >= 0 && cp1[1] >= 0 && cp1[2] >= 0) {
+                                wall_coef<T>(k3(cp1), A, Bc, Cm, Cp);
+                                acc += A * U(d, cp1[0], cp1[1], cp1[2]);
+                            }
+                            if (cm2[0] >= 0 && cm2[1] >= 0 && cm2[2] >= 0) {
+                                wall_coef<T>(k3(cm2), A, Bc, Cm, Cp);
+                                acc += Cp * U(d, cm2[0], cm2[1], cm2[2]);
+                            }
+                            if (cp2[0] >= 0 && cp2[1] >= 0 && cp2[2] >= 0) {
+                                wall_coef<T>(k3(cp2), A, Bc, Cm, Cp);
+                                acc += Cm * U(d, cp2[0], cp2[1], cp2[2]);
+                            }
+                            return acc;
+                        };
+                        if (d != 0) {
+                            const int a[3] = {xm2, y, z}, b1[3] = {xm1, y, z}, b2[3] = {xp1, y, z}, b3[3] = {xp2, y, z};
+                            lap += trans(0, a, b1, b2, b3);
+                        }
+                        if (d != 1) {
+                            const int a[3] = {x, ym2, z}, b1[3] = {x, ym1, z}, b2[3] = {x, yp1, z}, b3[3] = {x, yp2, z};
+                            lap += trans(1, a, b1, b2, b3);
+                        }
+                        if (d != 2) {
+                            const int a[3] = {x, y, zm2}, b1[3] = {x, y, zm1}, b2[3] = {x, y, zp1}, b3[3] = {x, y, zp2};
+                            lap += trans(2, a, b1, b2, b3);
+                        }
+                    }
                     // the +d cell exists and is pore because the node is fluid
                     int ex = d == 0 ? xp1 : x, ey = d == 1 ? yp1 : y, ez = d == 2 ? zp1 : z;
                     if (B.alpha) lap -= T(0.5) * (B.alpha[c] + B.alpha[lin(ex, ey, ez)]) * u0;
@@ -273,6 +337,48 @@ __global__ void accumulate_kernel(double *__restrict__ u64, double *__restrict__
         if (threadIdx.x < 3)
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
         partials[blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------------------------ sensitivity
+// dJ/d alpha_c = scale * sum_{i,j} w_ij sum over the six faces F of cell c of v^(i)_F u^(j)_F
+// with u^(j) the forward and v^(i) the transposed (adjoint) solutions; scale carries
+// -1 / (2 Re^2 N) and the length units of k.
+template <typename T>
+struct SensArgs {
+    const T *fwd[3];  // u fields (3N) of the forward solves, nullptr if unused
+    const T *adj[3];  // u fields (3N) of the adjoint solves
+    double w[3][3];
+};
+
+template <typename T>
+__global__ void sensitivity_kernel(const SensArgs<T> A, int nx, int ny, int nz, int px, int py, int pz,
+                                   double scale, float *__restrict__ out) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx);
+        const long long r = c / nx;
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        const int xm = nb_coord(x - 1, nx, px), ym = nb_coord(y - 1, ny, py), zm = nb_coord(z - 1, nz, pz);
+        const long long lower[3] = {
+            xm >= 0 ? (long long)xm + (long long)nx * ((long long)y + (long long)ny * z) : -1,
+            ym >= 0 ? (long long)x + (long long)nx * ((long long)ym + (long long)ny * z) : -1,
+            zm >= 0 ? (long long)x + (long long)nx * ((long long)y + (long long)ny * zm) : -1};
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            if (!A.adj[i]) continue;
+            for (int j = 0; j < 3; ++j) {
+                if (!A.fwd[j] || A.w[i][j] == 0.0) continue;
+                double t = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    t += (double)A.adj[i][d * N + c] * (double)A.fwd[j][d * N + c];
+                    if (lower[d] >= 0) t += (double)A.adj[i][d * N + lower[d]] * (double)A.fwd[j][d * N + lower[d]];
+                }
+                s += A.w[i][j] * t;
+            }
+        }
+        out[c] = (float)(scale * s);
     }
 }
 

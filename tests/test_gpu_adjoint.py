@@ -1,0 +1,94 @@
+"""GPU adjoint sensitivity (pm_sensitivity, KTensorFn) against the oracle's adjoint.
+
+The oracle's adjoint is itself pinned by finite differences and the dot-product
+identity (tests/test_oracle_adjoint.py).  Tolerances: FP64 fields 1e-8 of the largest
+|dJ| (converged to 1e-12 on both sides); FP32 fields 2e-4 (FP32 solution and a sum of
+products over six faces)."""
+import numpy as np
+import pytest
+
+from paper_2407_19868_gb300 import geometry as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2407_19868_gb300 import api as A
+    A.load()
+    return A
+
+
+@pytest.fixture(scope="module")
+def case():
+    mask = G.overlapping_spheres((10, 12, 16), 2.5, 0.62, seed=51)
+    alpha = (G.rng(52).random(mask.shape) * 0.3).astype(np.float32)
+    w = np.zeros((3, 3))
+    w[0, 0], w[1, 0], w[0, 1], w[2, 2] = 1.0, 0.5, -0.3, 0.8
+    return mask, alpha, w
+
+
+@pytest.mark.parametrize("precision,tol,rel", [("fp64", 1e-12, 1e-8), ("fp32", 1e-9, 2e-4)])
+def test_sensitivity_matches_oracle(api, oracle_mod, case, precision, tol, rel):
+    mask, alpha, w = case
+    dJ_o, J_o, k_o = oracle_mod.sensitivity(mask, w, alpha=alpha.astype(np.float64), tol=1e-13)
+    r = api.sensitivity(mask, w, alpha=torch.from_numpy(alpha).cuda(), precision=precision, tol=tol)
+    assert r["status"] == api.PM_OK
+    dJ = r["dJ"].double().cpu().numpy()
+    scale = np.abs(dJ_o).max()
+    np.testing.assert_allclose(dJ, dJ_o, rtol=0, atol=rel * scale)
+    assert r["J"] == pytest.approx(J_o, rel=max(rel, 1e-9))
+    # solid voxels with no fluid face have zero sensitivity
+    nf, _ = oracle_mod.Domain(mask).tables()
+    touch = np.zeros(mask.shape, bool)
+    for d in range(3):
+        touch |= nf[d].astype(bool) | np.roll(nf[d].astype(bool), 1, axis=2 - d)
+    assert np.all(dJ[~touch] == 0.0)
+
+
+def test_symmetric_identity_on_gpu(api):
+    """Channels of width <= 2 voxels: cases 1, 2, 3, 6 only, symmetric stencil, so
+    dk_xx/d alpha = -(1/(2 Re^2 N)) sum over faces u_x-solution^2 (face products)."""
+    m = np.ones((4, 6, 8), dtype=np.uint8)
+    m[:, 1:3, :] = 0
+    m[1:3, :, 4] = 0
+    w = np.zeros((3, 3))
+    w[0, 0] = 1.0
+    r = api.sensitivity(m, w, precision="fp64", tol=1e-13)
+    s = api.solve_direction(m, 0, precision="fp64", tol=1e-13)
+    U = s["u"].double().cpu().numpy() * 0.01  # Darcy-scaled (1/Re) -> iteration units
+    ss = np.zeros(m.shape)
+    for d in range(3):
+        prod = U[d] * U[d]
+        ss += prod + np.roll(prod, 1, axis=2 - d)
+    expect = -ss / (2 * 0.01**2 * m.size)
+    np.testing.assert_allclose(r["dJ"].double().cpu().numpy(), expect, rtol=0, atol=1e-6 * np.abs(expect).max())
+
+
+def test_ktensor_autograd(api, oracle_mod, case):
+    mask, alpha, _ = case
+    KTensorFn = api.KTensorFn
+    a = torch.from_numpy(alpha).cuda().requires_grad_(True)
+    opts = {"precision": "fp64", "tol": 1e-12}
+    k = KTensorFn.apply(a, mask, opts)
+    _, k_o, _ = oracle_mod.ktensor(mask, tol=1e-13, alpha=alpha.astype(np.float64))
+    np.testing.assert_allclose(k.cpu().numpy(), k_o, rtol=0, atol=1e-9 * np.abs(k_o).max())
+    g = torch.zeros(3, 3, dtype=torch.float64, device="cuda")
+    g[0, 0], g[2, 1] = 1.0, 0.5
+    (k * g).sum().backward()
+    grad = a.grad.double().cpu().numpy()
+    # central differences of the same forward at three pore voxels
+    pore = np.argwhere(mask == 0)
+    for c in pore[G.rng(53).choice(len(pore), 3, replace=False)]:
+        h = 1e-3
+        ap, am = alpha.copy(), alpha.copy()
+        ap[tuple(c)] += h
+        am[tuple(c)] -= h
+        kp = KTensorFn.apply(torch.from_numpy(ap).cuda(), mask, opts).cpu().numpy()
+        km = KTensorFn.apply(torch.from_numpy(am).cuda(), mask, opts).cpu().numpy()
+        fd = (kp[0, 0] - km[0, 0] + 0.5 * (kp[2, 1] - km[2, 1])) / (2 * h)
+        assert grad[tuple(c)] == pytest.approx(fd, rel=2e-3, abs=1e-6 * np.abs(grad).max())
