@@ -1,9 +1,10 @@
 """GPU adjoint sensitivity (pm_sensitivity, KTensorFn) against the oracle's adjoint.
 
 The oracle's adjoint is itself pinned by finite differences and the dot-product
-identity (tests/test_oracle_adjoint.py).  Tolerances: FP64 fields 1e-8 of the largest
-|dJ| (converged to 1e-12 on both sides); FP32 fields 2e-4 (FP32 solution and a sum of
-products over six faces)."""
+identity (tests/test_oracle_adjoint.py).  Tolerances: FP64 fields 2e-7 of the largest
+|dJ| (both sides converged to 1e-12; the ABI returns dJ/d alpha as FP32, whose rounding
+is 6e-8 relative); FP32 fields 2e-4 (FP32 solution and a sum of products over six
+faces)."""
 import numpy as np
 import pytest
 
@@ -32,7 +33,7 @@ def case():
     return mask, alpha, w
 
 
-@pytest.mark.parametrize("precision,tol,rel", [("fp64", 1e-12, 1e-8), ("fp32", 1e-9, 2e-4)])
+@pytest.mark.parametrize("precision,tol,rel", [("fp64", 1e-12, 2e-7), ("fp32", 1e-9, 2e-4)])
 def test_sensitivity_matches_oracle(api, oracle_mod, case, precision, tol, rel):
     mask, alpha, w = case
     dJ_o, J_o, k_o = oracle_mod.sensitivity(mask, w, alpha=alpha.astype(np.float64), tol=1e-13)
@@ -76,7 +77,7 @@ def test_ktensor_autograd(api, oracle_mod, case):
     opts = {"precision": "fp64", "tol": 1e-12}
     k = KTensorFn.apply(a, mask, opts)
     _, k_o, _ = oracle_mod.ktensor(mask, tol=1e-13, alpha=alpha.astype(np.float64))
-    np.testing.assert_allclose(k.cpu().numpy(), k_o, rtol=0, atol=1e-9 * np.abs(k_o).max())
+    np.testing.assert_allclose(k.detach().cpu().numpy(), k_o, rtol=0, atol=1e-9 * np.abs(k_o).max())
     g = torch.zeros(3, 3, dtype=torch.float64, device="cuda")
     g[0, 0], g[2, 1] = 1.0, 0.5
     (k * g).sum().backward()
