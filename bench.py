@@ -250,7 +250,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}"},
         "k_tensor": [[float(v) for v in row] for row in k],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": stored_traffic(), "peak_kind": peak_kind,
                      "kernel": "fused pseudo-time sweep (3 drives per launch)",
                      "sweep_ms": sweep_ms, "alg_bytes_per_launch": alg_bytes},
         "cpu_baseline": cpu,
@@ -267,18 +267,42 @@ def run_ours(args):
 
 
 def run_profile_case(args):
-    """A short run of the sweep kernel on the benchmark mask for ncu captures: one drive,
-    FP32 fields, ``--profile-iters`` iterations through pm_iterate."""
+    """A short run in the benchmark's launch configuration for ncu captures: the same
+    mask, three drives batched per sweep launch, FP32 fields, stopped after
+    ``--profile-iters`` iterations (windows of 2 sweeps)."""
     import torch
     from paper_2407_19868_gb300 import api
     api.load()
     mask, _ = make_mask()
-    u = torch.zeros((3,) + mask.shape, dtype=torch.float32, device="cuda")
-    p = torch.zeros(mask.shape, dtype=torch.float32, device="cuda")
-    api.iterate(torch.from_numpy(mask).cuda(), u, p, args.profile_iters, drive_dir=0, precision="fp32")
+    r = api.permeability_tensor(torch.from_numpy(mask).cuda(), tol=1e-12, check_every=2,
+                                max_iter=args.profile_iters, precision="fp32")
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "pm_iterate", "iters": args.profile_iters, "mean_ux": float(u[0].mean())}))
+    print(json.dumps({"profile_case": "pm_permeability_tensor", "iters": r["stats"][0]["iters"],
+                      "status": r["status"]}))
     return 0
+
+
+def kernel_source_sha():
+    """SHA-256 of the sweep kernel's source, to tie stored ncu counters to a version."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pm_sweep_tiled.cuh", "pm_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2407_19868_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def stored_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_tiled_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel_source_sha256") == kernel_source_sha():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
 
 
 def main():
@@ -294,7 +318,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=300)
     ap.add_argument("--ref-iters", type=int, default=5)
     ap.add_argument("--profile-iters", type=int, default=0,
-                    help="profiling case: run this many pm_iterate iterations (one drive, FP32) on the mask and exit")
+                    help="profiling case: this many iterations of the benchmark solve, then exit")
     args = ap.parse_args()
     if args.profile_iters > 0:
         return run_profile_case(args)
