@@ -6,11 +6,6 @@
 
 namespace pmgb {
 
-// Bit offset of the 3-bit wall code of node u_d across axis i in a stencil code word.
-__host__ __device__ constexpr int pmgb_code_shift(int d, int i) {
-    return d == 0 ? (i == 1 ? 4 : 7) : d == 1 ? (i == 0 ? 10 : 13) : (i == 0 ? 16 : 19);
-}
-
 // ------------------------------------------------------------------ neighbourhood
 // Algorithm 1 "Evaluate neighborhood": per cell the pore flag and the fluid flags of its
 // three +d face nodes (Sec. 4: a face between two pore cells carries flow; every face
@@ -70,7 +65,7 @@ __device__ __forceinline__ T perp_d2(T u0, T um2, T um1, T up1, T up2, bool Fm2,
     return Fm2 ? (T(2) * um1 - T(5) * u0 - c15 * um2) : (c83 * um1 - c163 * u0);
 }
 
-// Coefficients of the 3-bit wall code (kind, side) of the tiled kernel's stencil codes:
+// Coefficients of the 3-bit wall code (kind, side) of a stencil code word:
 // the second derivative across the flow of node b is
 //   A (u(b-1) + u(b+1)) + B u(b) + Cm u(b-2) + Cp u(b+2).
 template <typename T>
@@ -168,7 +163,7 @@ __global__ void __launch_bounds__(256) sweep_simple_kernel(const SweepBatch<T> B
                         // transpose: sum over b = a + m e_i of b's coefficient for offset -m
                         auto trans = [&](int i, const int cm2[3], const int cm1[3], const int cp1[3],
                                          const int cp2[3]) -> T {
-                            const int sh = pmgb_code_shift(d, i);
+                            const int sh = code_shift(d, i);
                             auto k3 = [&](const int q[3]) -> uint32_t {
                                 return (B.code[lin(q[0], q[1], q[2])] >> sh) & 7u;
                             };

@@ -20,18 +20,7 @@
 namespace pmgb {
 
 // ------------------------------------------------------------------ stencil codes
-// bit 0          cell is pore
-// bits 1..3      node u_x, u_y, u_z fluid
-// 3-bit fields   wall case of node u_d along perpendicular axis i (Appendix B), stored as
-//                kind (bits 0-1) and side (bit 2):
-//                  kind 0  case 6, both neighbours fluid      u(-1) + u(+1) - 2 u0
-//                  kind 1  case 1, walls at -1/2 and +1/2     -8 u0
-//                  kind 2  cases 4/5, one wall, node at +-2   2 u(+-1) - 5 u0 - u(+-2) / 5
-//                  kind 3  cases 2/3, one wall, no node at +-2 (8 u(+-1) - 16 u0) / 3
-//                  side 1  the fluid side is + (cases 2, 4); 0 otherwise
-__host__ __device__ constexpr int code_shift(int d, int i) {
-    return d == 0 ? (i == 1 ? 4 : 7) : d == 1 ? (i == 0 ? 10 : 13) : (i == 0 ? 16 : 19);
-}
+// (layout: see code_shift in pm_common.cuh)
 
 __device__ __forceinline__ bool cell_pore(const uint8_t *mask, int x, int y, int z, int nx, int ny, int nz,
                                           const int per[3]) {
@@ -146,7 +135,13 @@ __device__ __forceinline__ Pair<uint32_t> ld2u(const uint32_t *p) {
     return *reinterpret_cast<const Pair<uint32_t> *>(p);
 }
 
-template <typename T, int MODE, bool REDUCE, bool SRC>
+// Byte offset of the coefficient-table entry of the wall code at shift sh of word c.
+template <typename T>
+__device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
+    return sizeof(WallCoef<T>) == 16 ? (c >> (sh - 4)) & 0x70u : ((c >> sh) & 7u) * (uint32_t)sizeof(WallCoef<T>);
+}
+
+template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
 __global__ void __launch_bounds__(kNT, 2)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int zchunk, int tiles_x,
                        int tiles_y) {
@@ -166,6 +161,7 @@ __global__ void __launch_bounds__(kNT, 2)
     const T *__restrict__ guy = P.uin + N;
     const T *__restrict__ guz = P.uin + 2 * N;
     const T *__restrict__ gp = P.pin;
+    const unsigned char *coef_bytes = reinterpret_cast<const unsigned char *>(S.coef);
 
     if (tid < 8) {
         // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3;
@@ -210,8 +206,8 @@ __global__ void __launch_bounds__(kNT, 2)
         const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
         if (gx >= 0 && gy >= 0) co = gx + nx * gy;
     }
-    auto issue_plane = [&](int k) {
-        TiledStage<T> &G = S.st[((k % kStages) + kStages) % kStages];
+    auto issue_plane = [&](int k, int slot) {
+        TiledStage<T> &G = S.st[slot];
         const int gz = nb_coord(k, nz, B.per[2]);
         const long long po = (long long)gz * plane;
 #pragma unroll
@@ -274,13 +270,19 @@ __global__ void __launch_bounds__(kNT, 2)
     for (int i = 0; i < 5; ++i) qx[i] = qy[i] = Pair<T>{T(0), T(0)};
 #pragma unroll
     for (int i = 0; i < 3; ++i) qz[i] = Pair<T>{T(0), T(0)};
-    Pair<T> pn_prev{T(0), T(0)}, pn_cur{T(0), T(0)};
+    Pair<T> pn_m{T(0), T(0)};  // own p^n on the plane being updated (m)
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 
     const int t0 = m0 - 2;
-    issue_plane(t0);
-    issue_plane(t0 + 1);
-    issue_plane(t0 + 2);
+    int s2 = ((t0 - 2) % kStages + kStages) % kStages;  // ring stages of planes t-2, t-1, t
+    int s1 = (s2 + 1) % kStages, s0 = (s2 + 2) % kStages;
+    {
+        int sl = s0;
+        for (int k = 0; k < 3; ++k) {
+            issue_plane(t0 + k, sl);
+            sl = sl == kStages - 1 ? 0 : sl + 1;
+        }
+    }
 
     // p^n of one cell at box position e of plane k (stage K), the plane below in KM
     auto press1 = [&](const TiledStage<T> &K, const TiledStage<T> &KM, int e, int k, long long g) -> T {
@@ -294,15 +296,26 @@ __global__ void __launch_bounds__(kNT, 2)
         const T pn = MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
         return (K.cd[e] & 1u) ? pn : T(0);
     };
+    // second derivative across the flow (Appendix B) from the 3-bit wall code, added to lap
+    auto perp = [&](T &lap, uint32_t cc, int sh, T um2, T um1, T u0, T up1, T up2) {
+        const WallCoef<T> w = *reinterpret_cast<const WallCoef<T> *>(coef_bytes + coef_offset<T>(cc, sh));
+        lap = fma(w.A, um1, lap);
+        lap = fma(w.A, up1, lap);
+        lap = fma(w.B, u0, lap);
+        lap = fma(w.Cm, um2, lap);
+        lap = fma(w.Cp, up2, lap);
+    };
 
-    int s2 = ((t0 - 2) % kStages + kStages) % kStages;  // ring stages of planes t-2, t-1, t
-    int s1 = (s2 + 1) % kStages, s0 = (s2 + 2) % kStages;
     T *outx = P.uout + (long long)m0 * plane + gin_own;
     T *outp = P.pout + (long long)m0 * plane + gin_own;
     for (int t = t0; t <= m1 + 1; ++t) {
         cp_async_wait<2>();
         __syncthreads();
-        issue_plane(t + 3);
+        {
+            int sl = s0 + 3;
+            if (sl >= kStages) sl -= kStages;
+            issue_plane(t + 3, sl);
+        }
         const TiledStage<T> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
         // z queues of the own column pair
 #pragma unroll
@@ -315,8 +328,8 @@ __global__ void __launch_bounds__(kNT, 2)
         qz[0] = qz[1];
         qz[1] = qz[2];
         qz[2] = ld2(&G1.uz[own]);
-        // p^n on plane t-1: own pair (its u values are in the queues) and halo cells
-        pn_prev = pn_cur;
+        // own p^n on plane t-1 (kept in registers until after the update of plane t-2)
+        Pair<T> pn_new;
         {
             const Pair<uint32_t> cd = ld2u<T>(&G1.cd[own]);
             const Pair<T> pin = ld2(&G1.pin[own]);
@@ -334,137 +347,134 @@ __global__ void __launch_bounds__(kNT, 2)
                 }
             }
             const bool pore0 = cd.a & 1u, pore1 = cd.b & 1u;
-            pn_cur.a = pore0 ? (MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0)) : T(0);
-            pn_cur.b = pore1 ? (MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1)) : T(0);
-            *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own]) = pn_cur;
+            pn_new.a = pore0 ? (MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0)) : T(0);
+            pn_new.b = pore1 ? (MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1)) : T(0);
             if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) {
                 dv0 = pore0 ? dv0 : T(0);
                 dv1 = pore1 ? dv1 : T(0);
                 acc[3] += (double)dv0 * (double)dv0 + (double)dv1 * (double)dv1;
             }
-            if (hrow) {
-                T *dst = &S.pn[(t - 1) & 1][hown];
-                dst[0] = press1(G1, G2, hown, t - 1, hg);
-                dst[1] = press1(G1, G2, hown + 1, t - 1, hg >= 0 ? hg + 1 : -1);
-            } else if (hcol) {
-                S.pn[(t - 1) & 1][hown] = press1(G1, G2, hown, t - 1, hg);
-            }
         }
         const int m = t - 2;
+        if (m >= m0 && real0) {
+            // ------------------------------------------------------ update on plane m
+            Pair<T> ux_n, uy_n, uz_n;
+            if (MODE == kModeP) {
+                ux_n = qx[2];
+                uy_n = qy[2];
+                uz_n = qz[1];
+            } else {
+                const Pair<uint32_t> c = ld2u<T>(&G2.cd[own]);
+                const T *PN = S.pn[m & 1];
+                const T *ux = G2.ux, *uy = G2.uy, *uz = G2.uz;
+                const long long gidx = (long long)m * plane + gin_own;
+                // u_x: along x (box), across y (box) and z (queue)
+                {
+                    const Pair<T> u0 = qx[2];
+                    const Pair<T> L = ld2(&ux[own - 2]), R = ld2(&ux[own + 2]);
+                    const Pair<T> ym2 = ld2(&ux[own - 2 * kBX]), ym1 = ld2(&ux[own - kBX]);
+                    const Pair<T> yp1 = ld2(&ux[own + kBX]), yp2 = ld2(&ux[own + 2 * kBX]);
+                    T lap0 = fma(T(-2), u0.a, u0.b + L.b);
+                    T lap1 = fma(T(-2), u0.b, R.a + u0.a);
+                    perp(lap0, c.a, code_shift(0, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
+                    perp(lap1, c.b, code_shift(0, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
+                    perp(lap0, c.a, code_shift(0, 2), qx[0].a, qx[1].a, u0.a, qx[3].a, qx[4].a);
+                    perp(lap1, c.b, code_shift(0, 2), qx[0].b, qx[1].b, u0.b, qx[3].b, qx[4].b);
+                    if (ALPHA) {
+                        lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + 1]) * u0.a;
+                        lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ex1_off]) * u0.b;
+                    }
+                    const T pr = PN[own + 2];
+                    T R0 = fma(B.inv_re, lap0, P.f[0] - (pn_m.b - pn_m.a));
+                    T R1 = fma(B.inv_re, lap1, P.f[0] - (pr - pn_m.b));
+                    if (SRC) {
+                        const Pair<T> sx = ld2(P.src + gidx);
+                        R0 += sx.a;
+                        R1 += sx.b;
+                    }
+                    ux_n.a = (c.a & node_bit(0)) ? fma(B.dt, R0, u0.a) : u0.a;
+                    ux_n.b = (c.b & node_bit(0)) ? fma(B.dt, R1, u0.b) : u0.b;
+                }
+                // u_y: along y (box), across x (box) and z (queue)
+                {
+                    const Pair<T> u0 = qy[2];
+                    const Pair<T> L = ld2(&uy[own - 2]), R = ld2(&uy[own + 2]);
+                    const Pair<T> ym1 = ld2(&uy[own - kBX]), yp1 = ld2(&uy[own + kBX]);
+                    T lap0 = fma(T(-2), u0.a, yp1.a + ym1.a);
+                    T lap1 = fma(T(-2), u0.b, yp1.b + ym1.b);
+                    perp(lap0, c.a, code_shift(1, 0), L.a, L.b, u0.a, u0.b, R.a);
+                    perp(lap1, c.b, code_shift(1, 0), L.b, u0.a, u0.b, R.a, R.b);
+                    perp(lap0, c.a, code_shift(1, 2), qy[0].a, qy[1].a, u0.a, qy[3].a, qy[4].a);
+                    perp(lap1, c.b, code_shift(1, 2), qy[0].b, qy[1].b, u0.b, qy[3].b, qy[4].b);
+                    if (ALPHA) {
+                        lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + ey_off]) * u0.a;
+                        lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ey_off]) * u0.b;
+                    }
+                    const Pair<T> pny = ld2(&PN[own + kBX]);
+                    T R0 = fma(B.inv_re, lap0, P.f[1] - (pny.a - pn_m.a));
+                    T R1 = fma(B.inv_re, lap1, P.f[1] - (pny.b - pn_m.b));
+                    if (SRC) {
+                        const Pair<T> sy = ld2(P.src + N + gidx);
+                        R0 += sy.a;
+                        R1 += sy.b;
+                    }
+                    uy_n.a = (c.a & node_bit(1)) ? fma(B.dt, R0, u0.a) : u0.a;
+                    uy_n.b = (c.b & node_bit(1)) ? fma(B.dt, R1, u0.b) : u0.b;
+                }
+                // u_z: along z (queue), across x and y (box)
+                {
+                    const Pair<T> u0 = qz[1];
+                    const Pair<T> L = ld2(&uz[own - 2]), R = ld2(&uz[own + 2]);
+                    const Pair<T> ym2 = ld2(&uz[own - 2 * kBX]), ym1 = ld2(&uz[own - kBX]);
+                    const Pair<T> yp1 = ld2(&uz[own + kBX]), yp2 = ld2(&uz[own + 2 * kBX]);
+                    T lap0 = fma(T(-2), u0.a, qz[2].a + qz[0].a);
+                    T lap1 = fma(T(-2), u0.b, qz[2].b + qz[0].b);
+                    perp(lap0, c.a, code_shift(2, 0), L.a, L.b, u0.a, u0.b, R.a);
+                    perp(lap1, c.b, code_shift(2, 0), L.b, u0.a, u0.b, R.a, R.b);
+                    perp(lap0, c.a, code_shift(2, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
+                    perp(lap1, c.b, code_shift(2, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
+                    if (ALPHA) {
+                        const int zp = nb_coord(m + 1, nz, B.per[2]);
+                        const long long g2 = (long long)(zp >= 0 ? zp : m) * plane + gin_own;
+                        lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0.a;
+                        lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[g2 + 1]) * u0.b;
+                    }
+                    T R0 = fma(B.inv_re, lap0, P.f[2] - (pn_new.a - pn_m.a));
+                    T R1 = fma(B.inv_re, lap1, P.f[2] - (pn_new.b - pn_m.b));
+                    if (SRC) {
+                        const Pair<T> sz = ld2(P.src + 2 * N + gidx);
+                        R0 += sz.a;
+                        R1 += sz.b;
+                    }
+                    uz_n.a = (c.a & node_bit(2)) ? fma(B.dt, R0, u0.a) : u0.a;
+                    uz_n.b = (c.b & node_bit(2)) ? fma(B.dt, R1, u0.b) : u0.b;
+                }
+            }
+            *reinterpret_cast<Pair<T> *>(outx) = ux_n;
+            *reinterpret_cast<Pair<T> *>(outx + N) = uy_n;
+            *reinterpret_cast<Pair<T> *>(outx + 2 * N) = uz_n;
+            *reinterpret_cast<Pair<T> *>(outp) = pn_m;
+            outx += plane;
+            outp += plane;
+            if (REDUCE) {
+                acc[0] += (double)ux_n.a + (double)ux_n.b;
+                acc[1] += (double)uy_n.a + (double)uy_n.b;
+                acc[2] += (double)uz_n.a + (double)uz_n.b;
+            }
+        }
+        // publish p^n of plane t-1 (own pair and halo cells) for the next step's update
+        *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own]) = pn_new;
+        if (hrow) {
+            T *dst = &S.pn[(t - 1) & 1][hown];
+            dst[0] = press1(G1, G2, hown, t - 1, hg);
+            dst[1] = press1(G1, G2, hown + 1, t - 1, hg >= 0 ? hg + 1 : -1);
+        } else if (hcol) {
+            S.pn[(t - 1) & 1][hown] = press1(G1, G2, hown, t - 1, hg);
+        }
+        pn_m = pn_new;
         s2 = s1;
         s1 = s0;
         s0 = s0 == kStages - 1 ? 0 : s0 + 1;
-        if (m < m0 || !real0) continue;
-        // ---------------------------------------------------------- update on plane m
-        Pair<T> ux_n, uy_n, uz_n;
-        if (MODE == kModeP) {
-            ux_n = qx[2];
-            uy_n = qy[2];
-            uz_n = qz[1];
-        } else {
-            const Pair<uint32_t> c = ld2u<T>(&G2.cd[own]);
-            const T *PN = S.pn[m & 1];
-            const T *ux = G2.ux, *uy = G2.uy, *uz = G2.uz;
-            // second derivative across the flow (Appendix B) from the 3-bit wall code
-            auto perp = [&](uint32_t cc, int shift, T um2, T um1, T u0, T up1, T up2) -> T {
-                const WallCoef<T> w = S.coef[(cc >> shift) & 7u];
-                return w.A * (um1 + up1) + w.B * u0 + w.Cm * um2 + w.Cp * up2;
-            };
-            const long long gidx = (long long)m * plane + gin_own;
-            const T fx = P.f[0], fy = P.f[1], fz = P.f[2];
-            // u_x: along x (box), across y (box) and z (queue)
-            {
-                const Pair<T> u0 = qx[2];
-                const Pair<T> L = ld2(&ux[own - 2]), R = ld2(&ux[own + 2]);
-                const Pair<T> ym2 = ld2(&ux[own - 2 * kBX]), ym1 = ld2(&ux[own - kBX]);
-                const Pair<T> yp1 = ld2(&ux[own + kBX]), yp2 = ld2(&ux[own + 2 * kBX]);
-                T lap0 = u0.b - T(2) * u0.a + L.b;
-                T lap1 = R.a - T(2) * u0.b + u0.a;
-                lap0 += perp(c.a, code_shift(0, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
-                lap1 += perp(c.b, code_shift(0, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
-                lap0 += perp(c.a, code_shift(0, 2), qx[0].a, qx[1].a, u0.a, qx[3].a, qx[4].a);
-                lap1 += perp(c.b, code_shift(0, 2), qx[0].b, qx[1].b, u0.b, qx[3].b, qx[4].b);
-                if (B.alpha) {
-                    lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + 1]) * u0.a;
-                    lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ex1_off]) * u0.b;
-                }
-                const T pr = PN[own + 2];
-                T R0 = B.inv_re * lap0 - (pn_prev.b - pn_prev.a) + fx;
-                T R1 = B.inv_re * lap1 - (pr - pn_prev.b) + fx;
-                if (SRC) {
-                    const Pair<T> sx = ld2(P.src + gidx);
-                    R0 += sx.a;
-                    R1 += sx.b;
-                }
-                ux_n.a = (c.a & node_bit(0)) ? u0.a + B.dt * R0 : u0.a;
-                ux_n.b = (c.b & node_bit(0)) ? u0.b + B.dt * R1 : u0.b;
-            }
-            // u_y: along y (box), across x (box) and z (queue)
-            {
-                const Pair<T> u0 = qy[2];
-                const Pair<T> L = ld2(&uy[own - 2]), R = ld2(&uy[own + 2]);
-                const Pair<T> ym1 = ld2(&uy[own - kBX]), yp1 = ld2(&uy[own + kBX]);
-                T lap0 = yp1.a - T(2) * u0.a + ym1.a;
-                T lap1 = yp1.b - T(2) * u0.b + ym1.b;
-                lap0 += perp(c.a, code_shift(1, 0), L.a, L.b, u0.a, u0.b, R.a);
-                lap1 += perp(c.b, code_shift(1, 0), L.b, u0.a, u0.b, R.a, R.b);
-                lap0 += perp(c.a, code_shift(1, 2), qy[0].a, qy[1].a, u0.a, qy[3].a, qy[4].a);
-                lap1 += perp(c.b, code_shift(1, 2), qy[0].b, qy[1].b, u0.b, qy[3].b, qy[4].b);
-                if (B.alpha) {
-                    lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + ey_off]) * u0.a;
-                    lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ey_off]) * u0.b;
-                }
-                const Pair<T> pny = ld2(&PN[own + kBX]);
-                T R0 = B.inv_re * lap0 - (pny.a - pn_prev.a) + fy;
-                T R1 = B.inv_re * lap1 - (pny.b - pn_prev.b) + fy;
-                if (SRC) {
-                    const Pair<T> sy = ld2(P.src + N + gidx);
-                    R0 += sy.a;
-                    R1 += sy.b;
-                }
-                uy_n.a = (c.a & node_bit(1)) ? u0.a + B.dt * R0 : u0.a;
-                uy_n.b = (c.b & node_bit(1)) ? u0.b + B.dt * R1 : u0.b;
-            }
-            // u_z: along z (queue), across x and y (box)
-            {
-                const Pair<T> u0 = qz[1];
-                const Pair<T> L = ld2(&uz[own - 2]), R = ld2(&uz[own + 2]);
-                const Pair<T> ym2 = ld2(&uz[own - 2 * kBX]), ym1 = ld2(&uz[own - kBX]);
-                const Pair<T> yp1 = ld2(&uz[own + kBX]), yp2 = ld2(&uz[own + 2 * kBX]);
-                T lap0 = qz[2].a - T(2) * u0.a + qz[0].a;
-                T lap1 = qz[2].b - T(2) * u0.b + qz[0].b;
-                lap0 += perp(c.a, code_shift(2, 0), L.a, L.b, u0.a, u0.b, R.a);
-                lap1 += perp(c.b, code_shift(2, 0), L.b, u0.a, u0.b, R.a, R.b);
-                lap0 += perp(c.a, code_shift(2, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
-                lap1 += perp(c.b, code_shift(2, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
-                if (B.alpha) {
-                    const int zp = nb_coord(m + 1, nz, B.per[2]);
-                    const long long g2 = (long long)(zp >= 0 ? zp : m) * plane + gin_own;
-                    lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0.a;
-                    lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[g2 + 1]) * u0.b;
-                }
-                T R0 = B.inv_re * lap0 - (pn_cur.a - pn_prev.a) + fz;
-                T R1 = B.inv_re * lap1 - (pn_cur.b - pn_prev.b) + fz;
-                if (SRC) {
-                    const Pair<T> sz = ld2(P.src + 2 * N + gidx);
-                    R0 += sz.a;
-                    R1 += sz.b;
-                }
-                uz_n.a = (c.a & node_bit(2)) ? u0.a + B.dt * R0 : u0.a;
-                uz_n.b = (c.b & node_bit(2)) ? u0.b + B.dt * R1 : u0.b;
-            }
-        }
-        *reinterpret_cast<Pair<T> *>(outx) = ux_n;
-        *reinterpret_cast<Pair<T> *>(outx + N) = uy_n;
-        *reinterpret_cast<Pair<T> *>(outx + 2 * N) = uz_n;
-        *reinterpret_cast<Pair<T> *>(outp) = pn_prev;
-        outx += plane;
-        outp += plane;
-        if (REDUCE) {
-            acc[0] += (double)ux_n.a + (double)ux_n.b;
-            acc[1] += (double)uy_n.a + (double)uy_n.b;
-            acc[2] += (double)uz_n.a + (double)uz_n.b;
-        }
     }
     cp_async_wait<0>();
     if (REDUCE) {
@@ -515,11 +525,11 @@ inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob) {
     return (long long)s.tiles_x * s.tiles_y * s.nzc;
 }
 
-template <typename T, int MODE, bool RED, bool SRC>
+template <typename T, int MODE, bool RED, bool SRC, bool ALPHA>
 inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, cudaStream_t s) {
     const TiledShape sh = tiled_shape(B.nx, B.ny, B.nz, B.nprob);
     const size_t smem = sizeof(TiledSmem<T>);
-    auto kern = sweep_tiled_kernel<T, MODE, RED, SRC>;
+    auto kern = sweep_tiled_kernel<T, MODE, RED, SRC, ALPHA>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -533,20 +543,27 @@ inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, 
     return cudaGetLastError();
 }
 
+template <typename T, int MODE>
+inline cudaError_t launch_tiled_m(const SweepBatch<T> &B, const uint32_t *code, bool red, bool src, cudaStream_t s) {
+    const bool alpha = B.alpha != nullptr;
+    if (red) {
+        if (src) return alpha ? launch_tiled_t<T, MODE, true, true, true>(B, code, s)
+                              : launch_tiled_t<T, MODE, true, true, false>(B, code, s);
+        return alpha ? launch_tiled_t<T, MODE, true, false, true>(B, code, s)
+                     : launch_tiled_t<T, MODE, true, false, false>(B, code, s);
+    }
+    if (src) return alpha ? launch_tiled_t<T, MODE, false, true, true>(B, code, s)
+                          : launch_tiled_t<T, MODE, false, true, false>(B, code, s);
+    return alpha ? launch_tiled_t<T, MODE, false, false, true>(B, code, s)
+                 : launch_tiled_t<T, MODE, false, false, false>(B, code, s);
+}
+
 template <typename T>
 inline int launch_tiled(const SweepBatch<T> &B, const uint32_t *code, int mode, bool red, bool src, cudaStream_t s) {
     cudaError_t e;
-#define PM_TL(M)                                                                            \
-    if (red) e = src ? launch_tiled_t<T, M, true, true>(B, code, s) : launch_tiled_t<T, M, true, false>(B, code, s); \
-    else e = src ? launch_tiled_t<T, M, false, true>(B, code, s) : launch_tiled_t<T, M, false, false>(B, code, s);
-    if (mode == kModeU) {
-        PM_TL(kModeU)
-    } else if (mode == kModePU) {
-        PM_TL(kModePU)
-    } else {
-        PM_TL(kModeP)
-    }
-#undef PM_TL
+    if (mode == kModeU) e = launch_tiled_m<T, kModeU>(B, code, red, src, s);
+    else if (mode == kModePU) e = launch_tiled_m<T, kModePU>(B, code, red, src, s);
+    else e = launch_tiled_m<T, kModeP>(B, code, red, src, s);
     return e == cudaSuccess ? 0 : (e == cudaErrorMemoryAllocation ? 6 : 7);
 }
 
