@@ -143,25 +143,18 @@ __device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
 
 template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
 __global__ void __launch_bounds__(kNT, 2)
-    sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int zchunk, int tiles_x,
-                       int tiles_y) {
+    sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int tiles_x, int tiles_y,
+                       long long per_cta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TiledSmem<T> &S = *reinterpret_cast<TiledSmem<T> *>(smem_raw);
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const long long N = B.N, plane = (long long)nx * ny;
     const int tid = threadIdx.x;
     const int lane = tid & 31, ty = tid >> 5;
-    const int pi = blockIdx.x % B.nprob;
-    const int tile = blockIdx.x / B.nprob;
-    const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
-    const int m0 = blockIdx.y * zchunk;
-    const int m1 = min(m0 + zchunk, nz);
-    const SweepProblem<T> &P = B.prob[pi];
-    const T *__restrict__ gux = P.uin;
-    const T *__restrict__ guy = P.uin + N;
-    const T *__restrict__ guz = P.uin + 2 * N;
-    const T *__restrict__ gp = P.pin;
     const unsigned char *coef_bytes = reinterpret_cast<const unsigned char *>(S.coef);
+    __shared__ double red_sum[kMaxBatch][4];  // per drive: FP64 sums of this CTA
+    __shared__ double red[kNT / 32][4];
+    if (REDUCE && tid < kMaxBatch * 4) red_sum[tid / 4][tid % 4] = 0.0;
 
     if (tid < 8) {
         // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3;
@@ -175,6 +168,39 @@ __global__ void __launch_bounds__(kNT, 2)
         w.Cp = side ? c : T(0);
         S.coef[tid] = w;
     }
+
+    // Persistent CTAs over columns (a column = one drive on one x-y tile, all planes).
+    // Phase 1: rounds in which CTA b marches whole column r G + b, so that all CTAs are at
+    // the same plane and the tile halos they share are served by L2.  Phase 2: the
+    // remaining columns, column by column, split into equal contiguous plane ranges
+    // (short pieces, neighbouring columns again at similar planes).  Every CTA gets the
+    // same number of plane steps, with at most one restart of its plane pipeline.
+    const long long G = gridDim.x, C = (long long)B.nprob * tiles_x * tiles_y;
+    const long long rounds = C / G, rem_total = (C - rounds * G) * nz;
+    long long pos = (long long)blockIdx.x * per_cta;
+    const long long pos_end = min(rem_total, pos + per_cta);
+    for (long long it = 0;; ++it) {
+    long long col;
+    int m0, m1;
+    if (it < rounds) {
+        col = it * G + blockIdx.x;
+        m0 = 0;
+        m1 = nz;
+    } else {
+        if (pos >= pos_end) break;
+        col = rounds * G + pos / nz;
+        m0 = (int)(pos % nz);
+        m1 = (int)min((long long)nz, m0 + (pos_end - pos));
+        pos += m1 - m0;
+    }
+    const int pi = (int)(col % B.nprob);
+    const int tile = (int)(col / B.nprob);
+    const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
+    const SweepProblem<T> &P = B.prob[pi];
+    const T *__restrict__ gux = P.uin;
+    const T *__restrict__ guy = P.uin + N;
+    const T *__restrict__ guz = P.uin + 2 * N;
+    const T *__restrict__ gp = P.pin;
 
     // Copy plan.  Field boxes are kBY rows of FCH 16-byte chunks, the code box kBY rows
     // of CCH chunks; chunk starts are multiples of 4 cells (nx % 4 == 0), so a chunk
@@ -476,38 +502,55 @@ __global__ void __launch_bounds__(kNT, 2)
         s1 = s0;
         s0 = s0 == kStages - 1 ? 0 : s0 + 1;
     }
+    // drain this column's copies before the ring is reused
     cp_async_wait<0>();
     if (REDUCE) {
-        for (int k = 0; k < 4; ++k)
-            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-        __shared__ double red[kNT / 32][4];
+        for (int q = 0; q < 4; ++q)
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
         if (lane == 0)
-            for (int k = 0; k < 4; ++k) red[ty][k] = acc[k];
+            for (int q = 0; q < 4; ++q) red[ty][q] = acc[q];
         __syncthreads();
         if (tid < 4) {
             double sum = 0.0;
             for (int w = 0; w < kNT / 32; ++w) sum += red[w][tid];
-            const long long blk = (long long)tile * gridDim.y + blockIdx.y;
-            P.partials[blk * 4 + tid] = sum;
+            red_sum[pi][tid] += sum;
         }
     }
+    __syncthreads();
+    }  // persistent loop
+    if (REDUCE && tid < B.nprob * 4) B.prob[tid / 4].partials[blockIdx.x * 4 + (tid % 4)] = red_sum[tid / 4][tid % 4];
 }
 
 // ------------------------------------------------------------------ host helpers
 struct TiledShape {
-    int tiles_x, tiles_y, zchunk, nzc;
+    int tiles_x, tiles_y, grid;
+    long long per_cta;
 };
+
+// Persistent grid: two CTAs per SM (the occupancy the kernel is built for).
+inline int tiled_grid_size() {
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms <= 0) {
+            (void)cudaGetLastError();
+            sms = 152;
+        }
+        grid = 2 * sms;
+    }
+    return grid;
+}
 
 inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1) {
     TiledShape s;
     s.tiles_x = (nx + kTX - 1) / kTX;
     s.tiles_y = (ny + kTY - 1) / kTY;
-    // z chunks: long enough to amortise the 4-plane start-up, enough CTAs (all drives) for
-    // about four waves of 2 CTAs on each of the 152 SMs
-    int zc = 128;
-    while (zc > 8 && (long long)s.tiles_x * s.tiles_y * nprob * ((nz + zc - 1) / zc) < 152 * 2 * 4) zc /= 2;
-    s.zchunk = zc < nz ? zc : nz;
-    s.nzc = (nz + s.zchunk - 1) / s.zchunk;
+    s.grid = tiled_grid_size();
+    // plane steps per CTA in the second phase (columns left after whole rounds)
+    const long long C = (long long)nprob * s.tiles_x * s.tiles_y;
+    const long long rem = (C - (C / s.grid) * s.grid) * nz;
+    s.per_cta = (rem + s.grid - 1) / s.grid;
     return s;
 }
 
@@ -519,10 +562,10 @@ inline bool tiled_supported(int nx, int ny, int nz, int nprob) {
            (long long)nx * ny < (1ll << 31);
 }
 
+// Number of reduction partials per drive written by one launch (one per CTA).
 template <typename T>
-inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob) {
-    TiledShape s = tiled_shape(nx, ny, nz, nprob);
-    return (long long)s.tiles_x * s.tiles_y * s.nzc;
+inline long long tiled_num_blocks(int, int, int, int) {
+    return tiled_grid_size();
 }
 
 template <typename T, int MODE, bool RED, bool SRC, bool ALPHA>
@@ -538,8 +581,7 @@ inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid((unsigned)(sh.tiles_x * sh.tiles_y * B.nprob), (unsigned)sh.nzc, 1);
-    kern<<<grid, kNT, smem, s>>>(B, code, sh.zchunk, sh.tiles_x, sh.tiles_y);
+    kern<<<sh.grid, kNT, smem, s>>>(B, code, sh.tiles_x, sh.tiles_y, sh.per_cta);
     return cudaGetLastError();
 }
 
