@@ -108,10 +108,12 @@ struct TiledStage {
 };
 
 // Wall coefficients per 3-bit code (kind, side): the second derivative across the flow is
-// A (u(-1) + u(+1)) + B u0 + Cm u(-2) + Cp u(+2)  (non-fluid nodes hold 0).
+// A (u(-1) + u(+1)) + B u0 + C u(far), far = +2 if side else -2, with C = -1/5 for kind 2
+// (cases 4/5) and 0 otherwise (non-fluid nodes hold 0).  The table holds (A, B); the far
+// term is applied by selects on the code bits.
 template <typename T>
-struct alignas(4 * sizeof(T)) WallCoef {
-    T A, B, Cm, Cp;
+struct alignas(2 * sizeof(T)) WallCoef {
+    T A, B;
 };
 
 template <typename T>
@@ -138,7 +140,7 @@ __device__ __forceinline__ Pair<uint32_t> ld2u(const uint32_t *p) {
 // Byte offset of the coefficient-table entry of the wall code at shift sh of word c.
 template <typename T>
 __device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
-    return sizeof(WallCoef<T>) == 16 ? (c >> (sh - 4)) & 0x70u : ((c >> sh) & 7u) * (uint32_t)sizeof(WallCoef<T>);
+    return sizeof(WallCoef<T>) == 8 ? (c >> (sh - 3)) & 0x38u : ((c >> sh) & 7u) * (uint32_t)sizeof(WallCoef<T>);
 }
 
 template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
@@ -159,13 +161,10 @@ __global__ void __launch_bounds__(kNT, 2)
     if (tid < 8) {
         // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3;
         // side selects which +-2 node the one-sided cases use
-        const int kind = tid & 3, side = tid >> 2;
+        const int kind = tid & 3;
         WallCoef<T> w;
         w.A = kind == 0 ? T(1) : (kind == 2 ? T(2) : (kind == 3 ? T(8) / T(3) : T(0)));
         w.B = kind == 0 ? T(-2) : (kind == 1 ? T(-8) : (kind == 2 ? T(-5) : T(-16) / T(3)));
-        const T c = kind == 2 ? T(-1) / T(5) : T(0);
-        w.Cm = side ? T(0) : c;
-        w.Cp = side ? c : T(0);
         S.coef[tid] = w;
     }
 
@@ -325,11 +324,11 @@ __global__ void __launch_bounds__(kNT, 2)
     // second derivative across the flow (Appendix B) from the 3-bit wall code, added to lap
     auto perp = [&](T &lap, uint32_t cc, int sh, T um2, T um1, T u0, T up1, T up2) {
         const WallCoef<T> w = *reinterpret_cast<const WallCoef<T> *>(coef_bytes + coef_offset<T>(cc, sh));
-        lap = fma(w.A, um1, lap);
-        lap = fma(w.A, up1, lap);
+        const uint32_t n = cc >> sh;
+        const T far = (n & 4u) ? up2 : um2;
+        lap = fma(w.A, um1 + up1, lap);
         lap = fma(w.B, u0, lap);
-        lap = fma(w.Cm, um2, lap);
-        lap = fma(w.Cp, up2, lap);
+        lap = fma(T(-1) / T(5), ((n & 3u) == 2u) ? far : T(0), lap);
     };
 
     T *outx = P.uout + (long long)m0 * plane + gin_own;
