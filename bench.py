@@ -174,7 +174,7 @@ def run_ours(args):
     n_fluid = int(np.count_nonzero(mask == 0))
     N = mask.size
     dmask = torch.from_numpy(mask).cuda()
-    opts = dict(tol=args.tol, precision=args.precision, check_every=args.check_every)
+    opts = dict(tol=args.tol, precision=args.precision, check_every=args.check_every, autotune=args.autotune)
 
     def barrier():
         if ws > 1:
@@ -275,7 +275,7 @@ def run_profile_case(args):
     api.load()
     mask, _ = make_mask()
     r = api.permeability_tensor(torch.from_numpy(mask).cuda(), tol=1e-12, check_every=2,
-                                max_iter=args.profile_iters, precision="fp32")
+                                max_iter=args.profile_iters, precision="fp32", autotune=args.autotune)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "pm_permeability_tensor", "iters": r["stats"][0]["iters"],
                       "status": r["status"]}))
@@ -316,7 +316,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=300)
-    ap.add_argument("--ref-iters", type=int, default=5)
+    ap.add_argument("--ref-iters", type=int, default=20)
+    ap.add_argument("--autotune", type=int, default=1, help="tune the sweep schedule in the first warm-up solve")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling case: this many iterations of the benchmark solve, then exit")
     args = ap.parse_args()

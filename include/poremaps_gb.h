@@ -99,7 +99,10 @@ typedef struct pm_options {
     double dc_switch_tol;     /* PM_FP32_DC64: leave plain FP32 sweeps at this change */
     int32_t dc_max_rounds;    /* PM_FP32_DC64: maximum correction rounds */
     int32_t kernel;           /* 0 = default sweep kernel, 1 = simple reference kernel */
-    int32_t reserved[8];
+    int32_t autotune;         /* 1: time the tiled kernel's schedules on the first sweeps of
+                                 the first solve of a shape and keep the fastest (those
+                                 sweeps are iterations of the solve and are counted) */
+    int32_t reserved[7];
 } pm_options;
 
 typedef struct pm_stats {
@@ -119,7 +122,7 @@ typedef struct pm_stats {
 
 /* Fills *opt with the defaults: tol 1e-6, check_every 200, max_iter 2e6,
  * PM_FP32_RED64, dt_safety 0.9, Re 0.01, c2 1.5e6, graphs on, percolation check on,
- * dc_switch_tol 1e-5, dc_max_rounds 8. */
+ * dc_switch_tol 1e-5, dc_max_rounds 8, autotune on. */
 PM_API void pm_default_options(pm_options *opt);
 
 /* Human-readable text of a pm_status (static storage). */

@@ -57,7 +57,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("dt_safety", C.c_double), ("Re", C.c_double),
                 ("c2", C.c_double), ("use_graph", C.c_int32), ("check_percolation", C.c_int32),
                 ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
-                ("reserved", C.c_int32 * 8)]
+                ("autotune", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class Stats(C.Structure):

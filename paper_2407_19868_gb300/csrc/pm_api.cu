@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -255,6 +256,7 @@ struct Solver {
     T dt = 0, dtc2 = 0, inv_re = 0;
     const T *alpha = nullptr;
     bool transposed = false;  // adjoint solves: transpose of the viscous operator
+    int zchunk = 0;           // tiled-kernel schedule (0 = persistent), set by tune()
 
     Solver(const Geometry &gg, const pm_options &oo, cudaStream_t ss, Scratch &sc)
         : g(gg), o(oo), s(ss), scr(sc) {}
@@ -273,11 +275,7 @@ struct Solver {
         inv_re = (T)(1.0 / o.Re);
         dim3 gr = grid();
         nblk = (long long)gr.x * gr.y * g.nz;
-        long long nblk_t = 0;
-        for (int k = 1; k <= kMaxBatch; ++k) {
-            const long long b = tiled_num_blocks<T>(g.nx, g.ny, g.nz, k);
-            nblk_t = b > nblk_t ? b : nblk_t;
-        }
+        const long long nblk_t = tiled_max_blocks<T>(g.nx, g.ny, g.nz, np);
         const long long nblk_max = nblk > nblk_t ? nblk : nblk_t;
         int st;
         for (int k = 0; k < nprob; ++k) {
@@ -351,7 +349,7 @@ struct Solver {
         bool has_src = false;
         for (int k = 0; k < nprob; ++k) has_src |= src[k] != nullptr;
         if (use_tiled()) {
-            int st = launch_tiled<T>(B, g.code, mode, reduce, has_src, s);
+            int st = launch_tiled<T>(B, g.code, mode, reduce, has_src, zchunk, s);
             if (st) return st;
         } else if (mode == kModeU) {
             reduce ? launch_simple<kModeU, true>(B, has_src) : launch_simple<kModeU, false>(B, has_src);
@@ -366,7 +364,7 @@ struct Solver {
     }
 
     long long reduce_blocks() const {
-        return use_tiled() ? tiled_num_blocks<T>(g.nx, g.ny, g.nz, nprob) : nblk;
+        return use_tiled() ? tiled_num_blocks<T>(g.nx, g.ny, g.nz, nprob, zchunk) : nblk;
     }
 
     int reduce_to_host_async() {
@@ -374,6 +372,53 @@ struct Solver {
         PM_CK(cudaGetLastError());
         PM_CK(cudaMemcpyAsync(hq, dq, sizeof(double) * nprob * 4, cudaMemcpyDeviceToHost, s));
         return PM_OK;
+    }
+
+    // Autotuner of the tiled kernel's schedule (persistent or plane chunks): times
+    // `reps` sweeps per candidate with CUDA events and keeps the fastest; the result is
+    // cached per (shape, drives, precision).  The timed sweeps are ordinary iterations
+    // of the solve (pairs, so the ping-pong parity is unchanged); returns their number.
+    int tune(int reps = 2) {
+        if (!use_tiled()) return 0;
+        static std::mutex mu;
+        static std::vector<std::array<long long, 6>> cache;  // nx, ny, nz, nprob, sizeof(T), zchunk
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            for (auto &c : cache)
+                if (c[0] == g.nx && c[1] == g.ny && c[2] == g.nz && c[3] == nprob && c[4] == (long long)sizeof(T)) {
+                    zchunk = (int)c[5];
+                    return 0;
+                }
+        }
+        int cand[8];
+        const int nc = tiled_candidates(g.nx, g.ny, g.nz, nprob, cand);
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        float best = 1e30f;
+        int best_zc = 0, done = 0;
+        for (int i = 0; i < nc; ++i) {
+            zchunk = cand[i];
+            cudaEventRecord(a, s);
+            for (int r = 0; r < 2 * reps; ++r)
+                if (sweep(kModePU, false)) break;
+            cudaEventRecord(b, s);
+            done += 2 * reps;
+            float ms = 0.f;
+            if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) {
+                best = ms;
+                best_zc = cand[i];
+            }
+        }
+        (void)cudaGetLastError();
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        zchunk = best_zc;
+        std::lock_guard<std::mutex> lock(mu);
+        cache.push_back({g.nx, g.ny, g.nz, nprob, (long long)sizeof(T), zchunk});
+        return done;
     }
 
     // Reduction of the current state (a pressure-only pass would change p; instead run
@@ -450,6 +495,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
     int rc = S.sweep(kModeU, false);
     if (rc) status = rc;
     iters = 1;
+    if (!rc && o.autotune) iters += S.tune();
     bool done = status != PM_OK;
     bool use_graph = o.use_graph != 0;
     if (!done && use_graph) {
@@ -875,7 +921,7 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
         B.prob[0].partials = nullptr;
         int st;
         if (tiled_supported<T>(B.nx, B.ny, B.nz, 1)) {
-            if ((st = launch_tiled<T>(B, code, mode, false, false, s))) return st;
+            if ((st = launch_tiled<T>(B, code, mode, false, false, 0, s))) return st;
         } else {
             dim3 blk(32, 8, 1), grd((B.nx + 31) / 32, (B.ny + 7) / 8, (unsigned)B.nz);
             if (mode == kModeU) sweep_simple_kernel<T, kModeU, false, false><<<grd, blk, 0, s>>>(B);
@@ -1000,6 +1046,7 @@ void pm_default_options(pm_options *o) {
     o->dc_switch_tol = 1e-5;
     o->dc_max_rounds = 8;
     o->kernel = 0;
+    o->autotune = 1;
 }
 
 const char *pm_strerror(int s) {

@@ -93,7 +93,14 @@ __device__ __forceinline__ void cp_async_wait() {
 // (x0 + 2 lane + 1, y0 + ty).  Shared-memory boxes are BX = TX + 8 wide (x0 - 4 ..
 // x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4 high (y0 - 2 .. y0 + TY + 1); the
 // stencil needs +-2 in x and y.
-constexpr int kTX = 64, kTY = 8, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY, kStages = 6;
+constexpr int kTX = 64, kTY = 8, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY;
+// Ring of kStages planes: planes t-2, t-1, t are read in step t while the copies of the
+// next kAhead planes are in flight.
+constexpr int kStages = 4, kAhead = kStages - 3;
+// p^n is needed on box rows 2 .. kTY + 2 (tile rows and the +y halo row) only
+constexpr int kPNL = (kTY + 1) * kBX;
+// CTAs per SM the FP32 kernel is built for (registers and shared memory)
+constexpr int kMinBlocks = 3;
 constexpr int kNT = (kTX / 2) * kTY;
 
 // One ring stage: the five arrays of one plane, contiguous, so that every access is a
@@ -119,7 +126,7 @@ struct alignas(2 * sizeof(T)) WallCoef {
 template <typename T>
 struct TiledSmem {
     TiledStage<T> st[kStages];
-    T pn[2][kPL];
+    T pn[2][kPNL];  // index: box index - 2 kBX
     WallCoef<T> coef[8];
 };
 
@@ -144,9 +151,9 @@ __device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
 }
 
 template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
-__global__ void __launch_bounds__(kNT, 2)
+__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int tiles_x, int tiles_y,
-                       long long per_cta) {
+                       long long per_cta, int zchunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TiledSmem<T> &S = *reinterpret_cast<TiledSmem<T> *>(smem_raw);
     const int nx = B.nx, ny = B.ny, nz = B.nz;
@@ -174,14 +181,20 @@ __global__ void __launch_bounds__(kNT, 2)
     // remaining columns, column by column, split into equal contiguous plane ranges
     // (short pieces, neighbouring columns again at similar planes).  Every CTA gets the
     // same number of plane steps, with at most one restart of its plane pipeline.
+    // zchunk > 0 instead: one (column, plane chunk) unit per CTA, chunk-major order.
     const long long G = gridDim.x, C = (long long)B.nprob * tiles_x * tiles_y;
-    const long long rounds = C / G, rem_total = (C - rounds * G) * nz;
+    const long long rounds = zchunk > 0 ? 0 : C / G, rem_total = zchunk > 0 ? 0 : (C - rounds * G) * nz;
     long long pos = (long long)blockIdx.x * per_cta;
     const long long pos_end = min(rem_total, pos + per_cta);
     for (long long it = 0;; ++it) {
     long long col;
     int m0, m1;
-    if (it < rounds) {
+    if (zchunk > 0) {
+        if (it > 0) break;
+        col = blockIdx.x % C;
+        m0 = (int)(blockIdx.x / C) * zchunk;
+        m1 = min(nz, m0 + zchunk);
+    } else if (it < rounds) {
         col = it * G + blockIdx.x;
         m0 = 0;
         m1 = nz;
@@ -303,7 +316,7 @@ __global__ void __launch_bounds__(kNT, 2)
     int s1 = (s2 + 1) % kStages, s0 = (s2 + 2) % kStages;
     {
         int sl = s0;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < kAhead; ++k) {
             issue_plane(t0 + k, sl);
             sl = sl == kStages - 1 ? 0 : sl + 1;
         }
@@ -334,12 +347,12 @@ __global__ void __launch_bounds__(kNT, 2)
     T *outx = P.uout + (long long)m0 * plane + gin_own;
     T *outp = P.pout + (long long)m0 * plane + gin_own;
     for (int t = t0; t <= m1 + 1; ++t) {
-        cp_async_wait<2>();
+        cp_async_wait<kAhead - 1>();
         __syncthreads();
         {
-            int sl = s0 + 3;
+            int sl = s0 + kAhead;
             if (sl >= kStages) sl -= kStages;
-            issue_plane(t + 3, sl);
+            issue_plane(t + kAhead, sl);
         }
         const TiledStage<T> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
         // z queues of the own column pair
@@ -390,7 +403,7 @@ __global__ void __launch_bounds__(kNT, 2)
                 uz_n = qz[1];
             } else {
                 const Pair<uint32_t> c = ld2u<T>(&G2.cd[own]);
-                const T *PN = S.pn[m & 1];
+                const T *PN = S.pn[m & 1] - 2 * kBX;
                 const T *ux = G2.ux, *uy = G2.uy, *uz = G2.uz;
                 const long long gidx = (long long)m * plane + gin_own;
                 // u_x: along x (box), across y (box) and z (queue)
@@ -488,13 +501,13 @@ __global__ void __launch_bounds__(kNT, 2)
             }
         }
         // publish p^n of plane t-1 (own pair and halo cells) for the next step's update
-        *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own]) = pn_new;
+        *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own - 2 * kBX]) = pn_new;
         if (hrow) {
-            T *dst = &S.pn[(t - 1) & 1][hown];
+            T *dst = &S.pn[(t - 1) & 1][hown - 2 * kBX];
             dst[0] = press1(G1, G2, hown, t - 1, hg);
             dst[1] = press1(G1, G2, hown + 1, t - 1, hg >= 0 ? hg + 1 : -1);
         } else if (hcol) {
-            S.pn[(t - 1) & 1][hown] = press1(G1, G2, hown, t - 1, hg);
+            S.pn[(t - 1) & 1][hown - 2 * kBX] = press1(G1, G2, hown, t - 1, hg);
         }
         pn_m = pn_new;
         s2 = s1;
@@ -522,11 +535,11 @@ __global__ void __launch_bounds__(kNT, 2)
 
 // ------------------------------------------------------------------ host helpers
 struct TiledShape {
-    int tiles_x, tiles_y, grid;
+    int tiles_x, tiles_y, grid, zchunk;
     long long per_cta;
 };
 
-// Persistent grid: two CTAs per SM (the occupancy the kernel is built for).
+// Number of SMs of the current device (the persistent grid is a multiple of it).
 inline int tiled_grid_size() {
     static int grid = 0;
     if (!grid) {
@@ -536,21 +549,50 @@ inline int tiled_grid_size() {
             (void)cudaGetLastError();
             sms = 152;
         }
-        grid = 2 * sms;
+        grid = sms;
     }
     return grid;
 }
 
-inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1) {
+// Launch geometry.  zchunk = 0: persistent CTAs (kMinBlocks per SM, whole-column rounds
+// then equal plane ranges); zchunk > 0: one CTA per (column, chunk of zchunk planes).
+template <typename T>
+inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1, int zchunk = 0) {
     TiledShape s;
     s.tiles_x = (nx + kTX - 1) / kTX;
     s.tiles_y = (ny + kTY - 1) / kTY;
-    s.grid = tiled_grid_size();
-    // plane steps per CTA in the second phase (columns left after whole rounds)
     const long long C = (long long)nprob * s.tiles_x * s.tiles_y;
-    const long long rem = (C - (C / s.grid) * s.grid) * nz;
-    s.per_cta = (rem + s.grid - 1) / s.grid;
+    s.zchunk = zchunk > 0 ? (zchunk < nz ? zchunk : nz) : 0;
+    if (s.zchunk > 0) {
+        s.grid = (int)(C * ((nz + s.zchunk - 1) / s.zchunk));
+        s.per_cta = 0;
+    } else {
+        s.grid = tiled_grid_size() * (sizeof(T) == 4 ? kMinBlocks : 1);
+        // plane steps per CTA in the second phase (columns left after whole rounds)
+        const long long rem = (C - (C / s.grid) * s.grid) * nz;
+        s.per_cta = (rem + s.grid - 1) / s.grid;
+    }
     return s;
+}
+
+// Schedules the autotuner tries: persistent, and plane chunks giving about 3..8 CTAs of
+// work per resident CTA slot.
+inline int tiled_candidates(int nx, int ny, int nz, int nprob, int out[8]) {
+    int n = 0;
+    out[n++] = 0;
+    const long long C = (long long)nprob * ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY);
+    const long long slots = (long long)tiled_grid_size() * kMinBlocks;
+    for (int w = 3; w <= 8 && n < 8; ++w) {
+        long long chunks = (w * slots + C - 1) / C;
+        if (chunks < 1) chunks = 1;
+        int zc = (int)((nz + chunks - 1) / chunks);
+        if (zc < 12) zc = 12;
+        if (zc > nz) zc = nz;
+        bool dup = false;
+        for (int i = 0; i < n; ++i) dup |= out[i] == zc;
+        if (!dup) out[n++] = zc;
+    }
+    return n;
 }
 
 // The tiled kernel copies whole 16-byte chunks of 4 cells: x extents must be multiples
@@ -563,13 +605,26 @@ inline bool tiled_supported(int nx, int ny, int nz, int nprob) {
 
 // Number of reduction partials per drive written by one launch (one per CTA).
 template <typename T>
-inline long long tiled_num_blocks(int, int, int, int) {
-    return tiled_grid_size();
+inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob, int zchunk = 0) {
+    return tiled_shape<T>(nx, ny, nz, nprob, zchunk).grid;
+}
+
+// Largest grid over the autotuner's candidates (sizes the reduction buffers).
+template <typename T>
+inline long long tiled_max_blocks(int nx, int ny, int nz, int nprob) {
+    int cand[8];
+    const int n = tiled_candidates(nx, ny, nz, nprob, cand);
+    long long g = 0;
+    for (int i = 0; i < n; ++i) {
+        const long long b = tiled_num_blocks<T>(nx, ny, nz, nprob, cand[i]);
+        g = b > g ? b : g;
+    }
+    return g;
 }
 
 template <typename T, int MODE, bool RED, bool SRC, bool ALPHA>
-inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, cudaStream_t s) {
-    const TiledShape sh = tiled_shape(B.nx, B.ny, B.nz, B.nprob);
+inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, cudaStream_t s) {
+    const TiledShape sh = tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk);
     const size_t smem = sizeof(TiledSmem<T>);
     auto kern = sweep_tiled_kernel<T, MODE, RED, SRC, ALPHA>;
     static bool attr_set = false;  // per instantiation
@@ -580,31 +635,33 @@ inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    kern<<<sh.grid, kNT, smem, s>>>(B, code, sh.tiles_x, sh.tiles_y, sh.per_cta);
+    kern<<<sh.grid, kNT, smem, s>>>(B, code, sh.tiles_x, sh.tiles_y, sh.per_cta, sh.zchunk);
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
-inline cudaError_t launch_tiled_m(const SweepBatch<T> &B, const uint32_t *code, bool red, bool src, cudaStream_t s) {
+inline cudaError_t launch_tiled_m(const SweepBatch<T> &B, const uint32_t *code, bool red, bool src, int zc,
+                                  cudaStream_t s) {
     const bool alpha = B.alpha != nullptr;
     if (red) {
-        if (src) return alpha ? launch_tiled_t<T, MODE, true, true, true>(B, code, s)
-                              : launch_tiled_t<T, MODE, true, true, false>(B, code, s);
-        return alpha ? launch_tiled_t<T, MODE, true, false, true>(B, code, s)
-                     : launch_tiled_t<T, MODE, true, false, false>(B, code, s);
+        if (src) return alpha ? launch_tiled_t<T, MODE, true, true, true>(B, code, zc, s)
+                              : launch_tiled_t<T, MODE, true, true, false>(B, code, zc, s);
+        return alpha ? launch_tiled_t<T, MODE, true, false, true>(B, code, zc, s)
+                     : launch_tiled_t<T, MODE, true, false, false>(B, code, zc, s);
     }
-    if (src) return alpha ? launch_tiled_t<T, MODE, false, true, true>(B, code, s)
-                          : launch_tiled_t<T, MODE, false, true, false>(B, code, s);
-    return alpha ? launch_tiled_t<T, MODE, false, false, true>(B, code, s)
-                 : launch_tiled_t<T, MODE, false, false, false>(B, code, s);
+    if (src) return alpha ? launch_tiled_t<T, MODE, false, true, true>(B, code, zc, s)
+                          : launch_tiled_t<T, MODE, false, true, false>(B, code, zc, s);
+    return alpha ? launch_tiled_t<T, MODE, false, false, true>(B, code, zc, s)
+                 : launch_tiled_t<T, MODE, false, false, false>(B, code, zc, s);
 }
 
 template <typename T>
-inline int launch_tiled(const SweepBatch<T> &B, const uint32_t *code, int mode, bool red, bool src, cudaStream_t s) {
+inline int launch_tiled(const SweepBatch<T> &B, const uint32_t *code, int mode, bool red, bool src, int zchunk,
+                        cudaStream_t s) {
     cudaError_t e;
-    if (mode == kModeU) e = launch_tiled_m<T, kModeU>(B, code, red, src, s);
-    else if (mode == kModePU) e = launch_tiled_m<T, kModePU>(B, code, red, src, s);
-    else e = launch_tiled_m<T, kModeP>(B, code, red, src, s);
+    if (mode == kModeU) e = launch_tiled_m<T, kModeU>(B, code, red, src, zchunk, s);
+    else if (mode == kModePU) e = launch_tiled_m<T, kModePU>(B, code, red, src, zchunk, s);
+    else e = launch_tiled_m<T, kModeP>(B, code, red, src, zchunk, s);
     return e == cudaSuccess ? 0 : (e == cudaErrorMemoryAllocation ? 6 : 7);
 }
 

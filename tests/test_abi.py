@@ -65,7 +65,8 @@ def test_struct_layout_matches_header(lib, tmp_path):
     """ctypes mirrors of pm_domain / pm_options / pm_stats have the C compiler's layout."""
     import subprocess
     fields = {"pm_domain": (lib.Domain, ["nx", "mask", "voxel_size", "bc"]),
-              "pm_options": (lib.Options, ["tol", "max_iter", "precision", "c2", "dc_switch_tol", "kernel"]),
+              "pm_options": (lib.Options, ["tol", "max_iter", "precision", "c2", "dc_switch_tol", "kernel",
+                                           "autotune"]),
               "pm_stats": (lib.Stats, ["iters", "q", "sweep_ms", "status", "percolates"])}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "poremaps_gb.h"', "int main(void){"]
     for st, (_, fs) in fields.items():
