@@ -365,3 +365,39 @@ def crops(states, n_crops: int = 8, lo: int = 256, hi: int = 1024, seed: int = 1
         oy = int(g.integers(0, ny - cy + 1))
         out.append(np.ascontiguousarray(st[:, oy:oy + cy, ox:ox + cx]))
     return out
+
+
+def boolean_spheres_gpu(n: int, r_lo: float, r_hi: float, target_porosity: float, seed: int,
+                        device="cuda", chunk: int = 256):
+    """Large periodic Boolean model (overlapping spheres, radii U[r_lo, r_hi]) on an n^3
+    grid, rasterised on the GPU with torch.  The number of spheres is fixed in advance
+    from the Boolean-model relation  porosity = exp(-density * E[sphere volume]), so the
+    porosity is target_porosity up to sampling noise (the achieved value is returned).
+    Centres and radii come from the seeded NumPy stream.  Returns (torch uint8 mask on
+    ``device``, info)."""
+    import torch
+
+    g = rng(seed)
+    ev = 4.0 / 3.0 * np.pi * (r_hi**4 - r_lo**4) / (4.0 * (r_hi - r_lo))  # E[r^3] for uniform r
+    count = int(round(-np.log(target_porosity) * float(n) ** 3 / ev))
+    centres = g.random((count, 3)) * n
+    radii = r_lo + (r_hi - r_lo) * g.random(count)
+    mask = torch.zeros((n, n, n), dtype=torch.uint8, device=device)
+    R = int(np.ceil(r_hi)) + 1
+    off = torch.arange(-R, R + 1, device=device, dtype=torch.float64)
+    for s in range(0, count, chunk):
+        c = torch.as_tensor(centres[s:s + chunk], device=device)
+        r = torch.as_tensor(radii[s:s + chunk], device=device)
+        base = torch.floor(c - 0.5)  # voxel whose centre is just below the centre
+        # candidate voxel indices per axis: base + off; centre distance (idx + 1/2 - c)
+        ix = base[:, None, :] + off[None, :, None]          # [k, 2R+1, 3]
+        dd = ix + 0.5 - c[:, None, :]
+        d2 = dd[:, :, None, None, 2] ** 2 + dd[:, None, :, None, 1] ** 2 + dd[:, None, None, :, 0] ** 2
+        inside = d2 <= (r * r)[:, None, None, None]
+        k, a, b, cc = torch.nonzero(inside, as_tuple=True)
+        iz = torch.remainder(ix[k, a, 2], n).long()
+        iy = torch.remainder(ix[k, b, 1], n).long()
+        ixx = torch.remainder(ix[k, cc, 0], n).long()
+        mask[iz, iy, ixx] = 1
+    phi = 1.0 - float(mask.float().mean())
+    return mask, {"spheres": count, "porosity": phi}
