@@ -159,6 +159,20 @@ def run_reference(args):
     return 0
 
 
+def aggregate_ranks(seconds: float, updates: float, device="cpu"):
+    """Whole-job figures over replicas: the slowest rank's time and the sum of the voxel
+    updates of all ranks (no collective on the data path; only this one at the end)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, updates
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args):
     import torch
 
@@ -199,15 +213,7 @@ def run_ours(args):
     dev_ms = e0.elapsed_time(e1)
     iters = [r["stats"][0]["iters"] for r in results]
     updates = sum(n_fluid * it * 3 for it in iters)
-    t_max = dev_ms / 1e3
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_max, float(updates)], dtype=torch.float64, device="cuda")
-        tt = torch.tensor([t_max], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        u = torch.tensor([float(updates)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        t_max, updates = float(tt.item()), float(u.item())
+    t_max, updates = aggregate_ranks(dev_ms / 1e3, float(updates), device="cuda")
     value = updates / t_max
 
     # end to end through the C ABI with host buffers (mask in host memory, k back to host)

@@ -222,3 +222,17 @@ def test_config2_ktensor_against_oracle_reference(api):
         ko = np.array(col["k_col"])
         kg = r["k_raw"][:, int(j)]
         np.testing.assert_allclose(kg, ko, rtol=1e-5, atol=0)
+
+
+def test_divergence_and_iteration_limit_are_reported(api):
+    """Failure detection on the host: a pseudo-time step five times the stability bound
+    blows the iteration up (a finite overflow to Inf/NaN, no device fault) and comes back
+    as PM_ERR_DIVERGED; an iteration limit gives PM_ERR_NOT_CONVERGED with valid fields."""
+    mask = G.overlapping_spheres((16, 16, 16), 3.0, 0.6, seed=71)
+    with pytest.raises(api.PMError) as e:
+        api.solve_direction(mask, 0, dt_safety=5.0, check_every=50, max_iter=20000)
+    assert e.value.status == api.PM_ERR_DIVERGED
+    r = api.solve_direction(mask, 0, tol=1e-14, check_every=10, max_iter=51, autotune=0)
+    assert r["status"] == api.PM_ERR_NOT_CONVERGED
+    assert r["stats"]["iters"] == 51
+    assert bool(torch.isfinite(r["u"]).all())
