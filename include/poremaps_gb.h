@@ -186,6 +186,22 @@ PM_API int pm_solve_direction(const pm_domain *dom, int dir, double drive, const
 PM_API int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_options *opt,
                            double k_out[9], double k_raw[9], pm_stats st[3], void *cuda_stream);
 
+/* Permeability tensors of many geometries in one solve (e.g. the images of a clogging
+ * sequence, Sec. 7.3, and cropped sub-domains of uneven sizes): every (domain, drive)
+ * problem of Eq. (cases_pressure) is a member of each sweep launch, the windows run as one
+ * captured CUDA graph, and each problem stops sweeping when its criterion holds.  Problems
+ * are processed in groups of up to 64.
+ *   doms: host array of n_domains domains; every nx must be a multiple of 4 and all
+ *   domains must share the boundary conditions (else PM_ERR_UNSUPPORTED).
+ *   drives: host, n_domains bit masks (bit j = drive along e_(j+1)), or NULL / 0 for all.
+ *   k_out: host, 9 doubles per domain (row-major, symmetrised); k_raw: same, unsymmetrised,
+ *   or NULL.  st: host, 3 pm_stats per domain (per drive), or NULL.
+ *   Non-percolating or unrequested drives leave zero columns (PM_ERR_NOT_PERCOLATING is
+ *   returned if any requested drive does not percolate; the rest is computed).
+ *   Precision PM_FP32_RED64 or PM_FP64. */
+PM_API int pm_batch_ktensor(int n_domains, const pm_domain *doms, const int32_t *drives, const pm_options *opt,
+                            double *k_out, double *k_raw, pm_stats *st, void *cuda_stream);
+
 /* Adjoint sensitivity of J = sum_ij w_ij k_ij to a per-cell drag field alpha (not in the
  * paper: the steady momentum equation of Sec. 3 / 4 gains -(1/Re) alpha_f u with the face
  * value alpha_f = (alpha(c) + alpha(c+e_d)) / 2, alpha in units of mu / dx^2; alpha = 0 is

@@ -37,7 +37,8 @@ _PRECISION = {"fp32": FP32_RED64, "fp32_red64": FP32_RED64, "fp32_dc64": FP32_DC
 
 # every function the header declares (checked by the ABI test)
 EXPORTED = ["pm_default_options", "pm_strerror", "pm_version", "pm_time_step", "pm_iterate",
-            "pm_iterate_noalloc", "pm_solve_direction", "pm_permeability_tensor", "pm_sensitivity"]
+            "pm_iterate_noalloc", "pm_solve_direction", "pm_permeability_tensor", "pm_sensitivity",
+            "pm_batch_ktensor"]
 
 
 class PMError(RuntimeError):
@@ -108,6 +109,8 @@ def load():
         L.pm_permeability_tensor.argtypes = [C.POINTER(Domain), C.c_double, C.POINTER(Options), dp, dp,
                                              C.POINTER(Stats), vp]
         L.pm_sensitivity.argtypes = [C.POINTER(Domain), vp, dp, C.POINTER(Options), vp, dp, dp, vp]
+        L.pm_batch_ktensor.argtypes = [C.c_int, C.POINTER(Domain), C.POINTER(C.c_int32), C.POINTER(Options), dp, dp,
+                                       C.POINTER(Stats), vp]
         _LIB = L
         return L
 
@@ -247,6 +250,24 @@ def sensitivity(mask, w=None, alpha=None, dx: float = 1.0, bc=(0, 0, 0), stream=
                                dJ.data_ptr() if dJ is not None else None, C.byref(J), kr, _stream(stream))
     _check(st, "pm_sensitivity", soft=(PM_OK, PM_ERR_NOT_CONVERGED))
     return {"dJ": dJ, "J": float(J.value), "k_raw": np.array(kr[:]).reshape(3, 3), "status": st}
+
+
+def batch_ktensor(masks, drives=None, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts):
+    """Tensors of many geometries in one solve (pm_batch_ktensor).  masks: list of uint8
+    arrays / tensors; drives: per mask a bit mask of drive axes (None = all).  Returns
+    dict(k [n, 3, 3], k_raw [n, 3, 3], stats [n][3], status)."""
+    ms = [_Mask(m, dx=dx, bc=bc) for m in masks]
+    n = len(ms)
+    doms = (Domain * n)(*[m.dom for m in ms])
+    dr = (C.c_int32 * n)(*(drives if drives is not None else [0] * n))
+    o = options(**opts)
+    k = (C.c_double * (9 * n))()
+    kr = (C.c_double * (9 * n))()
+    s = (Stats * (3 * n))()
+    st = load().pm_batch_ktensor(n, doms, dr, C.byref(o), k, kr, s, _stream(stream))
+    _check(st, "pm_batch_ktensor", soft=(PM_OK, PM_ERR_NOT_PERCOLATING, PM_ERR_NOT_CONVERGED))
+    return {"k": np.array(k[:]).reshape(n, 3, 3), "k_raw": np.array(kr[:]).reshape(n, 3, 3),
+            "stats": [[s[3 * d + j].as_dict() for j in range(3)] for d in range(n)], "status": st}
 
 
 def _ktensor_fn():

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <array>
 #include <mutex>
 #include <utility>
@@ -249,7 +250,8 @@ struct Solver {
     int dir[kMaxBatch] = {0, 0, 0, 0};
     double force[kMaxBatch] = {0, 0, 0, 0};
     const T *src[kMaxBatch] = {nullptr, nullptr, nullptr, nullptr};
-    double *partials = nullptr;  // [nprob][nblk][4]
+    double *partials = nullptr;  // [nprob][nblk][4] (multi: [total_units][4])
+    long long unit_begin_h[kMaxBatch] = {};
     double *dq = nullptr;        // [nprob][4]
     double *hq = nullptr;        // pinned [nprob][4]
     long long nblk = 0;
@@ -257,6 +259,14 @@ struct Solver {
     const T *alpha = nullptr;
     bool transposed = false;  // adjoint solves: transpose of the viscous operator
     int zchunk = 0;           // tiled-kernel schedule (0 = persistent), set by tune()
+    // multi-geometry batch: problem k lives on geometry *geo[k]
+    bool multi = false;
+    const Geometry *geo[kMaxBatch] = {};
+    ReduceRange *ranges = nullptr;  // device, per problem
+    int *active = nullptr;          // device, per problem
+    int active_h[kMaxBatch] = {};
+    long long total_units = 0;
+    const Geometry &G(int k) const { return multi ? *geo[k] : g; }
 
     Solver(const Geometry &gg, const pm_options &oo, cudaStream_t ss, Scratch &sc)
         : g(gg), o(oo), s(ss), scr(sc) {}
@@ -279,15 +289,37 @@ struct Solver {
         const long long nblk_max = nblk > nblk_t ? nblk : nblk_t;
         int st;
         for (int k = 0; k < nprob; ++k) {
+            const long long Nk = G(k).N;
             for (int b = 0; b < 2; ++b) {
-                if ((st = scr.alloc(&F[k].u[b], (size_t)(3 * g.N)))) return st;
-                if ((st = scr.alloc(&F[k].p[b], (size_t)g.N))) return st;
-                PM_CK(cudaMemsetAsync(F[k].u[b], 0, sizeof(T) * 3 * g.N, s));
-                PM_CK(cudaMemsetAsync(F[k].p[b], 0, sizeof(T) * g.N, s));
+                if ((st = scr.alloc(&F[k].u[b], (size_t)(3 * Nk)))) return st;
+                if ((st = scr.alloc(&F[k].p[b], (size_t)Nk))) return st;
+                PM_CK(cudaMemsetAsync(F[k].u[b], 0, sizeof(T) * 3 * Nk, s));
+                PM_CK(cudaMemsetAsync(F[k].p[b], 0, sizeof(T) * Nk, s));
             }
             F[k].cur = 0;
         }
-        if ((st = scr.alloc(&partials, (size_t)(nprob * nblk_max * 4)))) return st;
+        if (multi) {
+            // one CTA per (column, plane chunk) of every problem; chunks of at most 64 planes
+            ReduceRange rh[kMaxBatch];
+            long long u = 0;
+            for (int k = 0; k < nprob; ++k) {
+                const Geometry &q = G(k);
+                const long long tiles = (long long)((q.nx + kTX - 1) / kTX) * ((q.ny + kTY - 1) / kTY);
+                const int zc = q.nz < 64 ? q.nz : 64;
+                unit_begin_h[k] = u;
+                rh[k] = {u, tiles * ((q.nz + zc - 1) / zc), (double)q.N};
+                u += rh[k].count;
+            }
+            total_units = u;
+            if ((st = scr.alloc(&partials, (size_t)(total_units * 4)))) return st;
+            if ((st = scr.alloc(&ranges, (size_t)nprob)) || (st = scr.alloc(&active, (size_t)nprob))) return st;
+            PM_CK(cudaMemcpyAsync(ranges, rh, sizeof(ReduceRange) * nprob, cudaMemcpyHostToDevice, s));
+            for (int k = 0; k < nprob; ++k) active_h[k] = 1;
+            PM_CK(cudaMemcpyAsync(active, active_h, sizeof(int) * nprob, cudaMemcpyHostToDevice, s));
+            PM_CK(cudaStreamSynchronize(s));
+        } else if ((st = scr.alloc(&partials, (size_t)(nprob * nblk_max * 4)))) {
+            return st;
+        }
         if ((st = scr.alloc(&dq, (size_t)(nprob * 4)))) return st;
         PM_CK(cudaMallocHost(&hq, sizeof(double) * nprob * 4));
         return PM_OK;
@@ -295,9 +327,9 @@ struct Solver {
 
     // Copy a caller state (same type, iteration units) into the current buffers.
     int load_state(int k, const T *u, const T *p) {
-        if (u) PM_CK(cudaMemcpyAsync(F[k].u[F[k].cur], u, sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
-        if (p) PM_CK(cudaMemcpyAsync(F[k].p[F[k].cur], p, sizeof(T) * g.N, cudaMemcpyDeviceToDevice, s));
-        sanitize_kernel<T><<<launch_grid(g.N), 256, 0, s>>>(g.flags, g.N, F[k].u[F[k].cur], F[k].p[F[k].cur]);
+        if (u) PM_CK(cudaMemcpyAsync(F[k].u[F[k].cur], u, sizeof(T) * 3 * G(k).N, cudaMemcpyDeviceToDevice, s));
+        if (p) PM_CK(cudaMemcpyAsync(F[k].p[F[k].cur], p, sizeof(T) * G(k).N, cudaMemcpyDeviceToDevice, s));
+        sanitize_kernel<T><<<launch_grid(G(k).N), 256, 0, s>>>(G(k).flags, G(k).N, F[k].u[F[k].cur], F[k].p[F[k].cur]);
         PM_CK(cudaGetLastError());
         return PM_OK;
     }
@@ -324,8 +356,22 @@ struct Solver {
             P.pout = F[k].p[1 - F[k].cur];
             P.src = src[k];
             for (int d = 0; d < 3; ++d) P.f[d] = (T)(d == dir[k] ? force[k] : 0.0);
-            P.partials = reduce ? partials + (size_t)k * reduce_blocks() * 4 : nullptr;
+            const Geometry &q = G(k);
+            P.code = q.code;
+            P.nx = q.nx;
+            P.ny = q.ny;
+            P.nz = q.nz;
+            P.zchunk = q.nz < 64 ? q.nz : 64;
+            P.tiles_x = (q.nx + kTX - 1) / kTX;
+            P.tiles_y = (q.ny + kTY - 1) / kTY;
+            P.unit_begin = unit_begin_h[k];
+            if (multi)
+                P.partials = reduce ? partials + (size_t)unit_begin_h[k] * 4 : nullptr;
+            else
+                P.partials = reduce ? partials + (size_t)k * reduce_blocks() * 4 : nullptr;
         }
+        B.multi = multi ? 1 : 0;
+        B.active = multi ? active : nullptr;
         return B;
     }
 
@@ -340,6 +386,7 @@ struct Solver {
     }
 
     bool use_tiled() const {
+        if (multi) return true;  // batches are built only from tiled-kernel shapes
         return o.kernel == 0 && !transposed && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
     }
 
@@ -368,7 +415,10 @@ struct Solver {
     }
 
     int reduce_to_host_async() {
-        reduce_partials_kernel<<<nprob, 256, 0, s>>>(partials, reduce_blocks(), g.N, dq);
+        if (multi)
+            reduce_ranges_kernel<<<nprob, 256, 0, s>>>(partials, ranges, dq);
+        else
+            reduce_partials_kernel<<<nprob, 256, 0, s>>>(partials, reduce_blocks(), g.N, dq);
         PM_CK(cudaGetLastError());
         PM_CK(cudaMemcpyAsync(hq, dq, sizeof(double) * nprob * 4, cudaMemcpyDeviceToHost, s));
         return PM_OK;
@@ -379,7 +429,7 @@ struct Solver {
     // cached per (shape, drives, precision).  The timed sweeps are ordinary iterations
     // of the solve (pairs, so the ping-pong parity is unchanged); returns their number.
     int tune(int reps = 2) {
-        if (!use_tiled()) return 0;
+        if (!use_tiled() || multi) return 0;
         static std::mutex mu;
         static std::vector<std::array<long long, 6>> cache;  // nx, ny, nz, nprob, sizeof(T), zchunk
         {
@@ -483,6 +533,8 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
     const RunCriterion &C = crit ? *crit : defc;
     int M = o.check_every + (o.check_every & 1);
     Monitor mon[kMaxBatch];
+    long long conv_iter[kMaxBatch];
+    for (int k = 0; k < kMaxBatch; ++k) conv_iter[k] = -1;
     int status = PM_OK;
     long long iters = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -547,6 +599,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
             if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) || !std::isfinite(q[3]))
                 bad = true;
             mon[k].update(q, S.dir[k], C.tol, C.ref[k]);
+            if (mon[k].converged && conv_iter[k] < 0) conv_iter[k] = iters;
             all = all && (mon[k].converged || (C.stop_on_stall && mon[k].stalled >= 6));
             if (st) {
                 st[k].div_res = std::sqrt(q[3]);
@@ -558,6 +611,23 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
             break;
         }
         if (all) break;
+        if (S.multi) {
+            // converged problems stop sweeping (even windows keep their buffer parity)
+            bool changed = false;
+            for (int k = 0; k < S.nprob; ++k) {
+                const int a = mon[k].converged ? 0 : 1;
+                changed |= a != S.active_h[k];
+                S.active_h[k] = a;
+            }
+            if (changed) {
+                cudaError_t e2 = cudaMemcpyAsync(S.active, S.active_h, sizeof(int) * S.nprob, cudaMemcpyHostToDevice, S.s);
+                if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(S.s);
+                if (e2 != cudaSuccess) {
+                    status = map_cuda(e2);
+                    break;
+                }
+            }
+        }
         if (iters >= C.max_iter) {
             status = PM_ERR_NOT_CONVERGED;
             break;
@@ -566,6 +636,11 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     // last half step: pressure of the last iteration, plus the sums of the final state
+    if (S.multi && (status == PM_OK || status == PM_ERR_NOT_CONVERGED)) {
+        for (int k = 0; k < S.nprob; ++k) S.active_h[k] = 1;
+        cudaError_t e2 = cudaMemcpyAsync(S.active, S.active_h, sizeof(int) * S.nprob, cudaMemcpyHostToDevice, S.s);
+        if (e2 != cudaSuccess) status = map_cuda(e2);
+    }
     if (status == PM_OK || status == PM_ERR_NOT_CONVERGED) {
         if ((rc = S.sweep(kModeP, true)) || (rc = S.reduce_to_host_async())) status = rc;
         else {
@@ -580,7 +655,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
     cudaEventDestroy(e1);
     if (st)
         for (int k = 0; k < S.nprob; ++k) {
-            st[k].iters = iters;
+            st[k].iters = (S.multi && conv_iter[k] >= 0) ? conv_iter[k] + 1 : iters;
             st[k].delta = mon[k].delta;
             st[k].err_est = mon[k].err;
             st[k].sweep_ms = win_sweeps ? win_ms / (double)win_sweeps : 0.0;
@@ -1026,6 +1101,81 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
     return st;
 }
 
+// Many geometries in one solve: every (domain, drive) problem is a member of each sweep
+// launch (one CTA per column chunk of each), windows are one captured graph, converged
+// problems are switched off through device flags.
+template <typename T>
+int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_options *o, double *k_out,
+               double *k_raw, pm_stats *st, cudaStream_t s, Scratch &scr, double t0) {
+    std::vector<Geometry> geos((size_t)nd);
+    struct Prob {
+        int d, j;
+    };
+    std::vector<Prob> probs;
+    int status = PM_OK;
+    for (int d = 0; d < nd; ++d) {
+        for (int i = 0; i < 9; ++i) {
+            k_out[9 * d + i] = 0.0;
+            if (k_raw) k_raw[9 * d + i] = 0.0;
+        }
+        std::vector<uint8_t> hm;
+        int rc = host_mask(&doms[d], hm);
+        if (rc) return rc;
+        if (!count_fluid(hm)) return PM_ERR_NO_FLUID;
+        const int per[3] = {doms[d].bc[0] == PM_BC_PERIODIC, doms[d].bc[1] == PM_BC_PERIODIC,
+                            doms[d].bc[2] == PM_BC_PERIODIC};
+        int perc[3] = {1, 1, 1};
+        if (o->check_percolation) percolation_host(hm, doms[d].nx, doms[d].ny, doms[d].nz, per, perc);
+        if ((rc = build_geometry(&doms[d], s, scr, geos[(size_t)d]))) return rc;
+        const int want = drives && drives[d] ? drives[d] : 7;
+        for (int j = 0; j < 3; ++j) {
+            if (st) {
+                std::memset(&st[3 * d + j], 0, sizeof(pm_stats));
+                st[3 * d + j].percolates = perc[j];
+            }
+            if (!(want & (1 << j))) continue;
+            if (!perc[j]) {
+                status = PM_ERR_NOT_PERCOLATING;
+                continue;
+            }
+            probs.push_back({d, j});
+        }
+    }
+    for (size_t g0 = 0; g0 < probs.size(); g0 += kMaxBatch) {
+        const int np = (int)std::min<size_t>(kMaxBatch, probs.size() - g0);
+        Solver<T> S(geos[(size_t)probs[g0].d], *o, s, scr);
+        S.multi = true;
+        for (int k = 0; k < np; ++k) {
+            S.geo[k] = &geos[(size_t)probs[g0 + k].d];
+            S.dir[k] = probs[g0 + k].j;
+            S.force[k] = 1.0;
+        }
+        int rc = S.init(np);
+        if (rc) return rc;
+        pm_stats bst[kMaxBatch];
+        std::memset(bst, 0, sizeof(bst));
+        rc = run_to_convergence<T>(S, bst, t0);
+        if (rc != PM_OK && rc != PM_ERR_NOT_CONVERGED) return rc;
+        if (rc == PM_ERR_NOT_CONVERGED && status == PM_OK) status = rc;
+        for (int k = 0; k < np; ++k) {
+            const int d = probs[g0 + k].d, j = probs[g0 + k].j;
+            const double dx2 = doms[d].voxel_size * doms[d].voxel_size;
+            for (int i = 0; i < 3; ++i) {
+                const double kij = bst[k].q[i] / o->Re * dx2;  // Appendix C, column j
+                if (k_raw) k_raw[9 * d + 3 * i + j] = kij;
+                k_out[9 * d + 3 * i + j] += 0.5 * kij;
+                k_out[9 * d + 3 * j + i] += 0.5 * kij;
+            }
+            if (st) {
+                const int perc = st[3 * d + j].percolates;
+                st[3 * d + j] = bst[k];
+                st[3 * d + j].percolates = perc;
+            }
+        }
+    }
+    return status;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -1152,6 +1302,34 @@ int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], 
     }
     cudaError_t e = cudaStreamSynchronize(ss.s);
     if (rc == PM_OK && e != cudaSuccess) rc = map_cuda(e);
+    return rc;
+}
+
+int pm_batch_ktensor(int n_domains, const pm_domain *doms, const int32_t *drives, const pm_options *o,
+                     double *k_out, double *k_raw, pm_stats *st, void *cuda_stream) {
+    if (n_domains < 1 || !doms || !k_out) return PM_ERR_INVALID_ARG;
+    int rc = validate_options(o);
+    if (rc) return rc;
+    if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
+    for (int d = 0; d < n_domains; ++d) {
+        if ((rc = validate_domain(&doms[d]))) return rc;
+        if (doms[d].nx % 4 != 0) return PM_ERR_UNSUPPORTED;
+        for (int a = 0; a < 3; ++a)
+            if (doms[d].bc[a] != doms[0].bc[a]) return PM_ERR_UNSUPPORTED;
+        if (drives && (drives[d] < 0 || drives[d] > 7)) return PM_ERR_INVALID_ARG;
+    }
+    const double t0 = now_s();
+    StreamScope ss(cuda_stream);
+    if (ss.status) return ss.status;
+    {
+        Scratch scr(ss.s);
+        if (o->precision == PM_FP64)
+            rc = batch_impl<double>(n_domains, doms, drives, o, k_out, k_raw, st, ss.s, scr, t0);
+        else
+            rc = batch_impl<float>(n_domains, doms, drives, o, k_out, k_raw, st, ss.s, scr, t0);
+    }
+    cudaError_t e = cudaStreamSynchronize(ss.s);
+    if ((rc == PM_OK || rc == PM_ERR_NOT_PERCOLATING) && e != cudaSuccess) rc = map_cuda(e);
     return rc;
 }
 

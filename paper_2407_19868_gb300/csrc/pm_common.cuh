@@ -54,9 +54,17 @@ struct SweepProblem {
     const T *src;    // 4N source (r_u x3, r_p) or nullptr
     T f[3];          // body force per face direction (the drive)
     double *partials;  // [nblocks][4] block sums (q_x, q_y, q_z, |div|^2) or nullptr
+    // geometry of this problem (multi-geometry batches; otherwise equal to the batch's)
+    const uint32_t *code;
+    int nx, ny, nz, zchunk;
+    int tiles_x, tiles_y;
+    long long unit_begin;  // first CTA of this problem in a multi-geometry launch
 };
 
-constexpr int kMaxBatch = 4;
+// Problems per sweep launch: up to kMaxSame drives on one geometry, or up to kMaxBatch
+// (geometry, drive) problems in a multi-geometry batch.
+constexpr int kMaxSame = 4;
+constexpr int kMaxBatch = 64;
 
 template <typename T>
 struct SweepBatch {
@@ -68,6 +76,8 @@ struct SweepBatch {
     const T *alpha;        // N per-cell drag or nullptr
     T inv_re, dt, dtc2;
     int nprob;
+    int multi;             // 1: problems have their own geometry (tiled kernel, one unit per CTA)
+    const int *active;     // device, per problem, 0 = skip (converged); nullptr = all active
     SweepProblem<T> prob[kMaxBatch];
 };
 

@@ -399,6 +399,32 @@ __global__ void reduce_partials_kernel(const double *partials, long long nblk, l
     }
 }
 
+// Per-problem window sums of a multi-geometry launch: problem k owns partials
+// [begin, begin + count) and has N cells; out[k][0..2] = q_d, out[k][3] = |D u|^2.
+struct ReduceRange {
+    long long begin, count;
+    double N;
+};
+
+__global__ void reduce_ranges_kernel(const double *partials, const ReduceRange *rr, double *out) {
+    const ReduceRange R = rr[blockIdx.x];
+    __shared__ double s[256][4];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long b = threadIdx.x; b < R.count; b += blockDim.x)
+        for (int k = 0; k < 4; ++k) a[k] += partials[(R.begin + b) * 4 + k];
+    for (int k = 0; k < 4; ++k) s[threadIdx.x][k] = a[k];
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int k = 0; k < 4; ++k) s[threadIdx.x][k] += s[threadIdx.x + st][k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) out[blockIdx.x * 4 + k] = s[0][k] / R.N;
+        out[blockIdx.x * 4 + 3] = s[0][3];
+    }
+}
+
 // y = a * x (type conversion allowed), n elements.
 template <typename TO, typename TI>
 __global__ void scale_copy_kernel(TO *__restrict__ y, const TI *__restrict__ x, double a, long long n) {

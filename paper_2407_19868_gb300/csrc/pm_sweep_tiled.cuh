@@ -154,16 +154,31 @@ template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
 __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int tiles_x, int tiles_y,
                        long long per_cta, int zchunk) {
+    // single geometry: B.nx.. and the arguments; multi-geometry: per problem (below)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TiledSmem<T> &S = *reinterpret_cast<TiledSmem<T> *>(smem_raw);
-    const int nx = B.nx, ny = B.ny, nz = B.nz;
-    const long long N = B.N, plane = (long long)nx * ny;
+    int nx = B.nx, ny = B.ny, nz = B.nz;
+    long long N = B.N, plane = (long long)nx * ny;
     const int tid = threadIdx.x;
     const int lane = tid & 31, ty = tid >> 5;
     const unsigned char *coef_bytes = reinterpret_cast<const unsigned char *>(S.coef);
-    __shared__ double red_sum[kMaxBatch][4];  // per drive: FP64 sums of this CTA
+    __shared__ double red_sum[kMaxSame][4];  // per drive: FP64 sums of this CTA
     __shared__ double red[kNT / 32][4];
-    if (REDUCE && tid < kMaxBatch * 4) red_sum[tid / 4][tid % 4] = 0.0;
+    if (REDUCE && tid < kMaxSame * 4) red_sum[tid / 4][tid % 4] = 0.0;
+    // multi-geometry launch: this CTA's problem (prefix table of CTA counts)
+    int mp = 0;
+    if (B.multi) {
+        while (mp + 1 < B.nprob && (long long)blockIdx.x >= B.prob[mp + 1].unit_begin) ++mp;
+        if (B.active && !B.active[mp]) return;
+        nx = B.prob[mp].nx;
+        ny = B.prob[mp].ny;
+        nz = B.prob[mp].nz;
+        plane = (long long)nx * ny;
+        N = plane * nz;
+        code = B.prob[mp].code;
+        tiles_x = B.prob[mp].tiles_x;
+        tiles_y = B.prob[mp].tiles_y;
+    }
 
     if (tid < 8) {
         // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3;
@@ -189,7 +204,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     for (long long it = 0;; ++it) {
     long long col;
     int m0, m1;
-    if (zchunk > 0) {
+    if (B.multi) {
+        // one (column, plane chunk) unit of problem mp, chunk-major
+        if (it > 0) break;
+        const long long lu = (long long)blockIdx.x - B.prob[mp].unit_begin;
+        const long long Cm = (long long)tiles_x * tiles_y;
+        const int zc = B.prob[mp].zchunk;
+        col = (long long)mp + B.nprob * (lu % Cm);  // decoded below as (drive mp, tile lu % Cm)
+        m0 = (int)(lu / Cm) * zc;
+        m1 = min(nz, m0 + zc);
+    } else if (zchunk > 0) {
         if (it > 0) break;
         col = blockIdx.x % C;
         m0 = (int)(blockIdx.x / C) * zchunk;
@@ -207,6 +231,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     }
     const int pi = (int)(col % B.nprob);
     const int tile = (int)(col / B.nprob);
+    const int rs = B.multi ? 0 : pi;  // slot of red_sum
     const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
     const SweepProblem<T> &P = B.prob[pi];
     const T *__restrict__ gux = P.uin;
@@ -525,12 +550,18 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         if (tid < 4) {
             double sum = 0.0;
             for (int w = 0; w < kNT / 32; ++w) sum += red[w][tid];
-            red_sum[pi][tid] += sum;
+            red_sum[rs][tid] += sum;
         }
     }
     __syncthreads();
     }  // persistent loop
-    if (REDUCE && tid < B.nprob * 4) B.prob[tid / 4].partials[blockIdx.x * 4 + (tid % 4)] = red_sum[tid / 4][tid % 4];
+    if (REDUCE) {
+        if (B.multi) {
+            if (tid < 4) B.prob[mp].partials[((long long)blockIdx.x - B.prob[mp].unit_begin) * 4 + tid] = red_sum[0][tid];
+        } else if (tid < B.nprob * 4) {
+            B.prob[tid / 4].partials[blockIdx.x * 4 + (tid % 4)] = red_sum[tid / 4][tid % 4];
+        }
+    }
 }
 
 // ------------------------------------------------------------------ host helpers
@@ -624,7 +655,11 @@ inline long long tiled_max_blocks(int nx, int ny, int nz, int nprob) {
 
 template <typename T, int MODE, bool RED, bool SRC, bool ALPHA>
 inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, cudaStream_t s) {
-    const TiledShape sh = tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk);
+    TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk);
+    if (B.multi) {
+        const SweepProblem<T> &L = B.prob[B.nprob - 1];
+        sh.grid = (int)(L.unit_begin + (long long)L.tiles_x * L.tiles_y * ((L.nz + L.zchunk - 1) / L.zchunk));
+    }
     const size_t smem = sizeof(TiledSmem<T>);
     auto kern = sweep_tiled_kernel<T, MODE, RED, SRC, ALPHA>;
     static bool attr_set = false;  // per instantiation

@@ -352,15 +352,17 @@ def clogging_sequence(nx: int = 1536, ny: int = 768, n_states: int = 24, phi0: f
     return states
 
 
-def crops(states, n_crops: int = 8, lo: int = 256, hi: int = 1024, seed: int = 100):
-    """Sub-domains of uneven in-plane sizes cut from randomly chosen states."""
+def crops(states, n_crops: int = 8, lo: int = 256, hi: int = 1024, seed: int = 100, multiple: int = 4):
+    """Sub-domains of uneven in-plane sizes cut from randomly chosen states; the sizes are
+    drawn uniformly in [lo, hi] (capped by the image) and rounded down to a multiple of
+    ``multiple`` voxels."""
     g = rng(seed)
     out = []
     for _ in range(n_crops):
         st = states[int(g.integers(len(states)))]
         nz, ny, nx = st.shape
-        cx = int(g.integers(lo, min(hi, nx) + 1))
-        cy = int(g.integers(lo, min(hi, ny) + 1))
+        cx = int(g.integers(lo, min(hi, nx) + 1)) // multiple * multiple
+        cy = int(g.integers(lo, min(hi, ny) + 1)) // multiple * multiple
         ox = int(g.integers(0, nx - cx + 1))
         oy = int(g.integers(0, ny - cy + 1))
         out.append(np.ascontiguousarray(st[:, oy:oy + cy, ox:ox + cx]))
