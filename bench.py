@@ -335,10 +335,11 @@ def run_sequence(args):
     gen_s = time.perf_counter() - t
     dmasks = [torch.from_numpy(m).cuda() for m in doms]
     res = []
-    for rep in range(2):  # first: autotuning-free warm-up of allocations
+    for max_iter in (201, args.seq_max_iter):  # a short warm-up, then the measured run
         torch.cuda.synchronize()
         t = time.perf_counter()
-        r = api.batch_ktensor(dmasks, drives=[3] * len(doms), tol=args.tol, precision="fp32")
+        r = api.batch_ktensor(dmasks, drives=[3] * len(doms), tol=args.tol, precision="fp32",
+                              max_iter=max_iter)
         torch.cuda.synchronize()
         res.append((time.perf_counter() - t, r))
     secs, r = res[-1]
@@ -350,6 +351,10 @@ def run_sequence(args):
             "generate_s": gen_s, "status": r["status"], "seconds_all_k": secs, "fluid_voxel_updates_per_s": upd / secs,
             "problems": sum(1 for d in range(len(doms)) for j in range(2) if r["stats"][d][j]["percolates"]),
             "iters": [[r["stats"][d][j]["iters"] for j in range(2)] for d in range(len(doms))],
+            "converged": [[r["stats"][d][j]["status"] == 0 for j in range(2)] for d in range(len(doms))],
+            "delta": [[r["stats"][d][j]["delta"] for j in range(2)] for d in range(len(doms))],
+            "max_iter": args.seq_max_iter,
+            "sweep_ms": r["stats"][0][0]["sweep_ms"],
             "k_xx": [float(r["k"][d][0, 0]) for d in range(len(doms))],
             "k_yy": [float(r["k"][d][1, 1]) for d in range(len(doms))],
             "porosity_2d": [float(np.count_nonzero(m[1:-1] == 0)) / m[1:-1].size for m in doms]}
@@ -396,6 +401,7 @@ def main():
     ap.add_argument("--large", type=int, default=0, help="large-domain measurement on an n^3 Boolean pack, then exit")
     ap.add_argument("--large-max-iter", type=int, default=40000)
     ap.add_argument("--sequence", action="store_true", help="batched precipitation-sequence measurement, then exit")
+    ap.add_argument("--seq-max-iter", type=int, default=4001)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling case: this many iterations of the benchmark solve, then exit")
     args = ap.parse_args()
