@@ -188,7 +188,8 @@ def run_ours(args):
     n_fluid = int(np.count_nonzero(mask == 0))
     N = mask.size
     dmask = torch.from_numpy(mask).cuda()
-    opts = dict(tol=args.tol, precision=args.precision, check_every=args.check_every, autotune=args.autotune)
+    opts = dict(tol=args.tol, precision=args.precision, check_every=args.check_every, autotune=args.autotune,
+                schedule=args.schedule)
 
     def barrier():
         if ws > 1:
@@ -251,6 +252,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "shape": list(SHAPE), "porosity": round(1 - mask.mean(), 6),
                    "seed": SEED, "drives": 3, "precision": args.precision, "tol": args.tol,
                    "check_every": args.check_every, "iters_per_step": iters,
+                   "schedule": results[-1]["stats"][0]["schedule"],
                    "seconds_to_k_tensor": dev_ms / 1e3 / args.steps,
                    "l2": "working set 1.6 GB of fields per sweep > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{ws}"},
@@ -281,10 +283,11 @@ def run_profile_case(args):
     api.load()
     mask, _ = make_mask()
     r = api.permeability_tensor(torch.from_numpy(mask).cuda(), tol=1e-12, check_every=2,
-                                max_iter=args.profile_iters, precision="fp32", autotune=args.autotune)
+                                max_iter=args.profile_iters, precision="fp32", autotune=args.autotune,
+                                schedule=args.schedule)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "pm_permeability_tensor", "iters": r["stats"][0]["iters"],
-                      "status": r["status"]}))
+                      "schedule": r["stats"][0]["schedule"], "status": r["status"]}))
     return 0
 
 
@@ -398,6 +401,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=300)
     ap.add_argument("--ref-iters", type=int, default=20)
     ap.add_argument("--autotune", type=int, default=1, help="tune the sweep schedule in the first warm-up solve")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="sweep schedule: 0 automatic, -1 persistent CTAs, n > 0 chunks of n planes")
     ap.add_argument("--large", type=int, default=0, help="large-domain measurement on an n^3 Boolean pack, then exit")
     ap.add_argument("--large-max-iter", type=int, default=40000)
     ap.add_argument("--sequence", action="store_true", help="batched precipitation-sequence measurement, then exit")

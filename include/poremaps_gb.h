@@ -102,7 +102,11 @@ typedef struct pm_options {
     int32_t autotune;         /* 1: time the tiled kernel's schedules on the first sweeps of
                                  the first solve of a shape and keep the fastest (those
                                  sweeps are iterations of the solve and are counted) */
-    int32_t reserved[7];
+    int32_t schedule;         /* tiled kernel's work split: 0 = automatic (the autotuner's
+                                 choice when autotune is set, else persistent CTAs),
+                                 -1 = persistent CTAs, n > 0 = one CTA per tile column
+                                 and chunk of n planes */
+    int32_t reserved[6];
 } pm_options;
 
 typedef struct pm_stats {
@@ -117,7 +121,9 @@ typedef struct pm_stats {
     int32_t dc_rounds;        /* defect-correction rounds done */
     int32_t status;           /* pm_status of this drive */
     int32_t percolates;       /* 1 if a fluid path wraps the domain along the drive */
-    int32_t reserved[5];
+    int32_t schedule;         /* tiled kernel's work split used (-1 persistent, n > 0 chunks
+                                 of n planes; 0 = simple kernel or multi-geometry batch) */
+    int32_t reserved[4];
 } pm_stats;
 
 /* Fills *opt with the defaults: tol 1e-6, check_every 200, max_iter 2e6,

@@ -58,21 +58,23 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("dt_safety", C.c_double), ("Re", C.c_double),
                 ("c2", C.c_double), ("use_graph", C.c_int32), ("check_percolation", C.c_int32),
                 ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
-                ("autotune", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("autotune", C.c_int32), ("schedule", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int64), ("q", C.c_double * 3), ("delta", C.c_double),
                 ("err_est", C.c_double), ("div_res", C.c_double), ("seconds", C.c_double),
                 ("sweep_ms", C.c_double), ("sweeps_timed", C.c_int64), ("dc_rounds", C.c_int32),
-                ("status", C.c_int32), ("percolates", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("status", C.c_int32), ("percolates", C.c_int32), ("schedule", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
     def as_dict(self):
         return {"iters": int(self.iters), "q": [float(v) for v in self.q], "delta": float(self.delta),
                 "err_est": float(self.err_est), "div_res": float(self.div_res),
                 "seconds": float(self.seconds), "sweep_ms": float(self.sweep_ms),
                 "sweeps_timed": int(self.sweeps_timed), "dc_rounds": int(self.dc_rounds),
-                "status": int(self.status), "percolates": bool(self.percolates)}
+                "status": int(self.status), "percolates": bool(self.percolates),
+                "schedule": int(self.schedule)}
 
 
 _LIB = None

@@ -135,6 +135,7 @@ int validate_options(const pm_options *o) {
     if (!(o->tol > 0) || o->check_every < 1 || o->max_iter < 1) return PM_ERR_INVALID_ARG;
     if (o->precision < PM_FP32_RED64 || o->precision > PM_FP64) return PM_ERR_INVALID_ARG;
     if (!(o->dt_safety > 0) || !(o->Re > 0) || !(o->c2 > 0)) return PM_ERR_INVALID_ARG;
+    if (o->schedule < -1) return PM_ERR_INVALID_ARG;
     return PM_OK;
 }
 
@@ -258,7 +259,7 @@ struct Solver {
     T dt = 0, dtc2 = 0, inv_re = 0;
     const T *alpha = nullptr;
     bool transposed = false;  // adjoint solves: transpose of the viscous operator
-    int zchunk = 0;           // tiled-kernel schedule (0 = persistent), set by tune()
+    int zchunk = 0;           // tiled-kernel schedule (0 = persistent), from the options or tune()
     // multi-geometry batch: problem k lives on geometry *geo[k]
     bool multi = false;
     const Geometry *geo[kMaxBatch] = {};
@@ -285,7 +286,12 @@ struct Solver {
         inv_re = (T)(1.0 / o.Re);
         dim3 gr = grid();
         nblk = (long long)gr.x * gr.y * g.nz;
-        const long long nblk_t = tiled_max_blocks<T>(g.nx, g.ny, g.nz, np);
+        zchunk = o.schedule > 0 ? o.schedule : 0;
+        long long nblk_t = tiled_max_blocks<T>(g.nx, g.ny, g.nz, np);
+        if (zchunk > 0) {
+            const long long b = tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, zchunk);
+            nblk_t = b > nblk_t ? b : nblk_t;
+        }
         const long long nblk_max = nblk > nblk_t ? nblk : nblk_t;
         int st;
         for (int k = 0; k < nprob; ++k) {
@@ -547,7 +553,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
     int rc = S.sweep(kModeU, false);
     if (rc) status = rc;
     iters = 1;
-    if (!rc && o.autotune) iters += S.tune();
+    if (!rc && o.autotune && o.schedule == 0) iters += S.tune();
     bool done = status != PM_OK;
     bool use_graph = o.use_graph != 0;
     if (!done && use_graph) {
@@ -662,6 +668,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
             st[k].sweeps_timed = win_sweeps;
             st[k].seconds = now_s() - t0;
             st[k].status = status;
+            st[k].schedule = S.use_tiled() && !S.multi ? (S.zchunk > 0 ? S.zchunk : -1) : 0;
         }
     return status;
 }
@@ -996,7 +1003,7 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
         B.prob[0].partials = nullptr;
         int st;
         if (tiled_supported<T>(B.nx, B.ny, B.nz, 1)) {
-            if ((st = launch_tiled<T>(B, code, mode, false, false, 0, s))) return st;
+            if ((st = launch_tiled<T>(B, code, mode, false, false, o->schedule > 0 ? o->schedule : 0, s))) return st;
         } else {
             dim3 blk(32, 8, 1), grd((B.nx + 31) / 32, (B.ny + 7) / 8, (unsigned)B.nz);
             if (mode == kModeU) sweep_simple_kernel<T, kModeU, false, false><<<grd, blk, 0, s>>>(B);

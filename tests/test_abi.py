@@ -59,6 +59,8 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert L.pm_permeability_tensor(C.byref(dom), 1.0, C.byref(o), k, None, None, None) == lib.PM_ERR_INVALID_ARG
     o = lib.options(tol=-1.0)
     assert L.pm_permeability_tensor(C.byref(dom), 1.0, C.byref(o), k, None, None, None) == lib.PM_ERR_INVALID_ARG
+    o = lib.options(schedule=-2)
+    assert L.pm_permeability_tensor(C.byref(dom), 1.0, C.byref(o), k, None, None, None) == lib.PM_ERR_INVALID_ARG
 
 
 def test_struct_layout_matches_header(lib, tmp_path):
@@ -66,8 +68,8 @@ def test_struct_layout_matches_header(lib, tmp_path):
     import subprocess
     fields = {"pm_domain": (lib.Domain, ["nx", "mask", "voxel_size", "bc"]),
               "pm_options": (lib.Options, ["tol", "max_iter", "precision", "c2", "dc_switch_tol", "kernel",
-                                           "autotune"]),
-              "pm_stats": (lib.Stats, ["iters", "q", "sweep_ms", "status", "percolates"])}
+                                           "autotune", "schedule"]),
+              "pm_stats": (lib.Stats, ["iters", "q", "sweep_ms", "status", "percolates", "schedule"])}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "poremaps_gb.h"', "int main(void){"]
     for st, (_, fs) in fields.items():
         src.append(f'printf("{st} %zu\\n", sizeof({st}));')
