@@ -22,15 +22,18 @@ __host__ __device__ constexpr int node_bit(int d) { return 2 << d; }
 // Stencil code word of a cell (computed once per geometry by code_kernel):
 //   bit 0        cell is pore
 //   bits 1..3    node u_x, u_y, u_z fluid
-//   nibbles      3-bit wall code of node u_d across axis i at bit code_shift(d, i):
+//   bits 4..21   3-bit wall code of node u_d across axis i at bit code_shift(d, i):
 //                kind (bits 0-1) and side (bit 2) of the Appendix B case
 //                  kind 0  case 6, both neighbours fluid      u(-1) + u(+1) - 2 u0
 //                  kind 1  case 1, walls at -1/2 and +1/2     -8 u0
 //                  kind 2  cases 4/5, one wall, node at +-2   2 u(+-1) - 5 u0 - u(+-2) / 5
 //                  kind 3  cases 2/3, one wall, no node at +-2 (8 u(+-1) - 16 u0) / 3
 //                  side 1  the fluid side is + (cases 2, 4); 0 otherwise
+//                The two codes of node u_d are adjacent: a 6-bit field at bit
+//                node_shift(d), the lower perpendicular axis in its low 3 bits.
+__host__ __device__ constexpr int node_shift(int d) { return 4 + 6 * d; }
 __host__ __device__ constexpr int code_shift(int d, int i) {
-    return d == 0 ? (i == 1 ? 4 : 8) : d == 1 ? (i == 0 ? 12 : 16) : (i == 0 ? 20 : 24);
+    return node_shift(d) + (i == (d == 0 ? 1 : 0) ? 0 : 3);
 }
 
 // Sweep variants.  The fused sweep works on the staggered state (u^n, p^{n-1}): it first

@@ -2,9 +2,9 @@
 //
 // A CTA owns a TX x TY column tile of the (x, y) plane and marches along z over a chunk
 // of planes.  Each plane of the five input arrays (u_x, u_y, u_z, p, stencil code) is
-// copied with its 2-voxel halo into a 6-stage shared-memory ring by cp.async, three
-// planes ahead of use, so each field value comes from DRAM once per sweep and the
-// neighbour reuse is served by shared memory (x, y) and per-thread register queues (z).
+// copied with its 2-voxel halo into a 4-stage shared-memory ring by cp.async, one plane
+// ahead of use, so each field value comes from DRAM once per sweep and the neighbour
+// reuse is served by shared memory (x, y) and per-thread register queues (z).
 //
 // Per step t the CTA
 //   reads plane t of its own column into the z queues,
@@ -97,37 +97,44 @@ constexpr int kTX = 64, kTY = 8, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY;
 // Ring of kStages planes: planes t-2, t-1, t are read in step t while the copies of the
 // next kAhead planes are in flight.
 constexpr int kStages = 4, kAhead = kStages - 3;
-// p^n is needed on box rows 2 .. kTY + 2 (tile rows and the +y halo row) only
-constexpr int kPNL = (kTY + 1) * kBX;
+// p^n, the input pressure and the stencil codes are needed on box rows 2 .. kTY + 2 (tile
+// rows and the +y halo row) only, u_y on rows 1 .. kTY + 2; u_x and u_z on all rows
+constexpr int kPNL = (kTY + 1) * kBX, kPNo = 2 * kBX;
+constexpr int kUYL = (kTY + 2) * kBX, kUYo = kBX;
 // CTAs per SM the FP32 kernel is built for (registers and shared memory)
 constexpr int kMinBlocks = 3;
 constexpr int kNT = (kTX / 2) * kTY;
 
 // One ring stage: the five arrays of one plane, contiguous, so that every access is a
-// per-step stage pointer plus a compile-time offset.
+// per-step stage pointer plus a compile-time offset.  Arrays that need fewer box rows
+// start at a later row: u_y at row 1 (index = box index - kUYo), p and the codes at
+// row 2 (index = box index - kPNo).
 template <typename T>
 struct TiledStage {
     T ux[kPL];
-    T uy[kPL];
     T uz[kPL];
-    T pin[kPL];
-    uint32_t cd[kPL];
+    T uy[kUYL];
+    T pin[kPNL];
+    uint32_t cd[kPNL];
 };
 
-// Wall coefficients per 3-bit code (kind, side): the second derivative across the flow is
-// A (u(-1) + u(+1)) + B u0 + C u(far), far = +2 if side else -2, with C = -1/5 for kind 2
-// (cases 4/5) and 0 otherwise (non-fluid nodes hold 0).  The table holds (A, B); the far
-// term is applied by selects on the code bits.
+// Wall coefficients per wall kind.  Non-fluid nodes hold 0, so with S = u(-1) + u(+1)
+// every Appendix B case is
+//   A (S - 2 u0) + K (u0 + u(far) / 5),   far = +2 if side else -2,
+//   case 6 (kind 0): A = 1;  case 1 (kind 1, S = 0): A = 4;  cases 2/3 (kind 3): A = 8/3;
+//   cases 4/5 (kind 2): A = 2, K = -1  (2 S - 5 u0 - u(far) / 5);  K = 0 otherwise.
+// One entry (A, K) is one 8-byte shared-memory load; the table is one bank row, so a
+// warp's lookups never conflict.
 template <typename T>
 struct alignas(2 * sizeof(T)) WallCoef {
-    T A, B;
+    T A, K;
 };
 
 template <typename T>
 struct TiledSmem {
     TiledStage<T> st[kStages];
     T pn[2][kPNL];  // index: box index - 2 kBX
-    WallCoef<T> coef[8];
+    WallCoef<T> coef[4];
 };
 
 // A pair of x-adjacent values (aligned for one 2-wide shared-memory access).
@@ -144,10 +151,13 @@ __device__ __forceinline__ Pair<uint32_t> ld2u(const uint32_t *p) {
     return *reinterpret_cast<const Pair<uint32_t> *>(p);
 }
 
-// Byte offset of the coefficient-table entry of the wall code at shift sh of word c.
+// Byte offset of the coefficient-table entry of the wall kind at bit sh of word c (one
+// shift and one mask: entries are 2 T, a power of two).
 template <typename T>
 __device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
-    return sizeof(WallCoef<T>) == 8 ? (c >> (sh - 3)) & 0x38u : ((c >> sh) & 7u) * (uint32_t)sizeof(WallCoef<T>);
+    constexpr int lg = sizeof(T) == 4 ? 3 : 4;
+    static_assert(sizeof(WallCoef<T>) == (1u << lg), "entry size");
+    return (c >> (sh - lg)) & (3u << lg);
 }
 
 template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
@@ -180,13 +190,12 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         tiles_y = B.prob[mp].tiles_y;
     }
 
-    if (tid < 8) {
-        // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3;
-        // side selects which +-2 node the one-sided cases use
-        const int kind = tid & 3;
+    if (tid < 4) {
+        // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3
+        const int kind = tid;
         WallCoef<T> w;
-        w.A = kind == 0 ? T(1) : (kind == 2 ? T(2) : (kind == 3 ? T(8) / T(3) : T(0)));
-        w.B = kind == 0 ? T(-2) : (kind == 1 ? T(-8) : (kind == 2 ? T(-5) : T(-16) / T(3)));
+        w.A = kind == 0 ? T(1) : (kind == 1 ? T(4) : (kind == 2 ? T(2) : T(8) / T(3)));
+        w.K = kind == 2 ? T(-1) : T(0);
         S.coef[tid] = w;
     }
 
@@ -247,25 +256,29 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     constexpr int FE = 16 / (int)sizeof(T), FCH = kBX / FE, CCH = kBX / 4;
     constexpr int FR = (FCH * kBY + kNT - 1) / kNT;
     int fo[FR], fs[FR];
-    bool fhas[FR];
+    bool fhas[FR], fuy[FR], fp[FR];  // chunk exists / row also holds u_y / also p
 #pragma unroll
     for (int r = 0; r < FR; ++r) {
         const int c = tid + r * kNT;
         fo[r] = -1;
         fs[r] = 0;
         fhas[r] = c < FCH * kBY;
+        fuy[r] = fp[r] = false;
         if (fhas[r]) {
             const int hy = c / FCH, hx = (c % FCH) * FE;
             fs[r] = hy * kBX + hx;
+            fuy[r] = hy >= 1 && hy <= kTY + 2;
+            fp[r] = hy >= 2 && hy <= kTY + 2;
             const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
             if (gx >= 0 && gy >= 0) fo[r] = gx + nx * gy;
         }
     }
+    // code chunks: box rows 2 .. kTY + 2; cs is the index in the stage's code array
     int co = -1, cs = 0;
-    const bool chas = tid < CCH * kBY;
+    const bool chas = tid < CCH * (kTY + 1);
     if (chas) {
-        const int hy = tid / CCH, hx = (tid % CCH) * 4;
-        cs = hy * kBX + hx;
+        const int hy = 2 + tid / CCH, hx = (tid % CCH) * 4;
+        cs = hy * kBX + hx - kPNo;
         const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
         if (gx >= 0 && gy >= 0) co = gx + nx * gy;
     }
@@ -280,16 +293,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             if (gz >= 0 && fo[r] >= 0) {
                 const long long o = po + fo[r];
                 cp_async16(&G.ux[e], gux + o);
-                cp_async16(&G.uy[e], guy + o);
                 cp_async16(&G.uz[e], guz + o);
-                cp_async16(&G.pin[e], gp + o);
+                if (fuy[r]) cp_async16(&G.uy[e - kUYo], guy + o);
+                if (fp[r]) cp_async16(&G.pin[e - kPNo], gp + o);
             } else {
 #pragma unroll
                 for (int j = 0; j < FE; ++j) {
                     G.ux[e + j] = T(0);
-                    G.uy[e + j] = T(0);
                     G.uz[e + j] = T(0);
-                    G.pin[e + j] = T(0);
+                    if (fuy[r]) G.uy[e - kUYo + j] = T(0);
+                    if (fp[r]) G.pin[e - kPNo + j] = T(0);
                 }
             }
         }
@@ -349,24 +362,23 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
 
     // p^n of one cell at box position e of plane k (stage K), the plane below in KM
     auto press1 = [&](const TiledStage<T> &K, const TiledStage<T> &KM, int e, int k, long long g) -> T {
-        const T dv = (K.ux[e] - K.ux[e - 1]) + (K.uy[e] - K.uy[e - kBX]) + (K.uz[e] - KM.uz[e]);
+        const T dv = (K.ux[e] - K.ux[e - 1]) + (K.uy[e - kUYo] - K.uy[e - kBX - kUYo]) + (K.uz[e] - KM.uz[e]);
         T rp = T(0);
         if (SRC && g >= 0) {
             const int gz = nb_coord(k, nz, B.per[2]);
             if (gz >= 0) rp = P.src[3 * N + (long long)gz * plane + g];
         }
-        const T p0 = K.pin[e];
+        const T p0 = K.pin[e - kPNo];
         const T pn = MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
-        return (K.cd[e] & 1u) ? pn : T(0);
+        return (K.cd[e - kPNo] & 1u) ? pn : T(0);
     };
     // second derivative across the flow (Appendix B) from the 3-bit wall code, added to lap
     auto perp = [&](T &lap, uint32_t cc, int sh, T um2, T um1, T u0, T up1, T up2) {
         const WallCoef<T> w = *reinterpret_cast<const WallCoef<T> *>(coef_bytes + coef_offset<T>(cc, sh));
         const uint32_t n = cc >> sh;
+        lap = fma(w.A, fma(T(-2), u0, um1 + up1), lap);
         const T far = (n & 4u) ? up2 : um2;
-        lap = fma(w.A, um1 + up1, lap);
-        lap = fma(w.B, u0, lap);
-        lap = fma(T(-1) / T(5), ((n & 3u) == 2u) ? far : T(0), lap);
+        lap = fma(w.K, fma(T(1) / T(5), far, u0), lap);
     };
 
     T *outx = P.uout + (long long)m0 * plane + gin_own;
@@ -387,16 +399,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             qy[i] = qy[i + 1];
         }
         qx[4] = ld2(&G0.ux[own]);
-        qy[4] = ld2(&G0.uy[own]);
+        qy[4] = ld2(&G0.uy[own - kUYo]);
         qz[0] = qz[1];
         qz[1] = qz[2];
         qz[2] = ld2(&G1.uz[own]);
         // own p^n on plane t-1 (kept in registers until after the update of plane t-2)
         Pair<T> pn_new;
         {
-            const Pair<uint32_t> cd = ld2u<T>(&G1.cd[own]);
-            const Pair<T> pin = ld2(&G1.pin[own]);
-            const Pair<T> uyd = ld2(&G1.uy[own - kBX]);
+            const Pair<uint32_t> cd = ld2u<T>(&G1.cd[own - kPNo]);
+            const Pair<T> pin = ld2(&G1.pin[own - kPNo]);
+            const Pair<T> uyd = ld2(&G1.uy[own - kBX - kUYo]);
             const T uxl = G1.ux[own - 1];
             T dv0 = (qx[3].a - uxl) + (qy[3].a - uyd.a) + (qz[2].a - qz[1].a);
             T dv1 = (qx[3].b - qx[3].a) + (qy[3].b - uyd.b) + (qz[2].b - qz[1].b);
@@ -427,8 +439,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 uy_n = qy[2];
                 uz_n = qz[1];
             } else {
-                const Pair<uint32_t> c = ld2u<T>(&G2.cd[own]);
-                const T *PN = S.pn[m & 1] - 2 * kBX;
+                const Pair<uint32_t> c = ld2u<T>(&G2.cd[own - kPNo]);
+                const T *PN = S.pn[m & 1];  // index: box index - 2 kBX
                 const T *ux = G2.ux, *uy = G2.uy, *uz = G2.uz;
                 const long long gidx = (long long)m * plane + gin_own;
                 // u_x: along x (box), across y (box) and z (queue)
@@ -447,7 +459,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                         lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + 1]) * u0.a;
                         lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ex1_off]) * u0.b;
                     }
-                    const T pr = PN[own + 2];
+                    const T pr = PN[own - 2 * kBX + 2];
                     T R0 = fma(B.inv_re, lap0, P.f[0] - (pn_m.b - pn_m.a));
                     T R1 = fma(B.inv_re, lap1, P.f[0] - (pr - pn_m.b));
                     if (SRC) {
@@ -461,8 +473,9 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 // u_y: along y (box), across x (box) and z (queue)
                 {
                     const Pair<T> u0 = qy[2];
-                    const Pair<T> L = ld2(&uy[own - 2]), R = ld2(&uy[own + 2]);
-                    const Pair<T> ym1 = ld2(&uy[own - kBX]), yp1 = ld2(&uy[own + kBX]);
+                    const int oy = own - kUYo;
+                    const Pair<T> L = ld2(&uy[oy - 2]), R = ld2(&uy[oy + 2]);
+                    const Pair<T> ym1 = ld2(&uy[oy - kBX]), yp1 = ld2(&uy[oy + kBX]);
                     T lap0 = fma(T(-2), u0.a, yp1.a + ym1.a);
                     T lap1 = fma(T(-2), u0.b, yp1.b + ym1.b);
                     perp(lap0, c.a, code_shift(1, 0), L.a, L.b, u0.a, u0.b, R.a);
@@ -473,7 +486,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                         lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + ey_off]) * u0.a;
                         lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ey_off]) * u0.b;
                     }
-                    const Pair<T> pny = ld2(&PN[own + kBX]);
+                    const Pair<T> pny = ld2(&PN[own - kBX]);
                     T R0 = fma(B.inv_re, lap0, P.f[1] - (pny.a - pn_m.a));
                     T R1 = fma(B.inv_re, lap1, P.f[1] - (pny.b - pn_m.b));
                     if (SRC) {
