@@ -31,6 +31,7 @@ _LIB = None
 
 PERIODIC = 0
 WALL = 1
+PRESSURE = 2  # fixed-pressure inlet/outlet reservoirs (first and last layer along the axis)
 
 # Sec. 4, "Simulation parametrization": Re = 0.01, c*^2 = 1.5e6, grad p = 1 / vx.
 RE_PAPER = 0.01
@@ -60,7 +61,7 @@ def build(force: bool = False) -> str:
 class _Params(C.Structure):
     _fields_ = [("Re", C.c_double), ("c2", C.c_double), ("dt", C.c_double),
                 ("f", C.c_double * 3), ("alpha", C.POINTER(C.c_double)),
-                ("transposed", C.c_int32)]
+                ("transposed", C.c_int32), ("p_res", C.c_double * 2)]
 
 
 def _lib():
@@ -123,7 +124,8 @@ def default_dt(Re: float = RE_PAPER, c2: float = C2_PAPER, safety: float = 0.9) 
 class Domain:
     """A voxel geometry with its neighbourhood evaluated (Algorithm 1,
     "Evaluate neighborhood").  ``mask`` is uint8 [nz][ny][nx], nonzero = solid;
-    ``bc`` per axis (x, y, z): PERIODIC or WALL."""
+    ``bc`` per axis (x, y, z): PERIODIC, WALL or PRESSURE (one axis at most, at least 3
+    cells: its first and last layer are the inlet and outlet reservoirs, Sec. 4)."""
 
     def __init__(self, mask: np.ndarray, bc=(PERIODIC, PERIODIC, PERIODIC)):
         m = np.ascontiguousarray(mask, dtype=np.uint8)
@@ -134,6 +136,12 @@ class Domain:
         nz, ny, nx = m.shape
         self.N = m.size
         self.bc = tuple(int(b) for b in bc)
+        pa = [a for a in range(3) if self.bc[a] == PRESSURE]
+        if len(pa) > 1:
+            raise ValueError("at most one fixed-pressure axis")
+        self.pax = pa[0] if pa else None
+        if self.pax is not None and (nx, ny, nz)[self.pax] < 3:
+            raise ValueError("a fixed-pressure axis needs at least 3 cells")
         bca = (C.c_int32 * 3)(*self.bc)
         self._L = _lib()
         self._ctx = self._L.or_ctx_create(nx, ny, nz, bca, m.ctypes.data_as(C.POINTER(C.c_uint8)))
@@ -156,10 +164,20 @@ class Domain:
 
     def _params(self, drive_dir, drive, Re, c2, dt, alpha, transposed):
         f = [0.0, 0.0, 0.0]
-        if drive_dir is not None:
+        pres = [0.0, 0.0]
+        if self.pax is not None:
+            # fixed-pressure drive: no body force, p_in - p_out = h (n_a - 1) around 0
+            if drive_dir is not None and drive_dir != self.pax:
+                raise ValueError("with a fixed-pressure axis the drive is along that axis")
+            if transposed:
+                raise ValueError("the transposed operator is not defined with fixed pressures")
+            if drive_dir is not None:
+                L = (self.shape[2], self.shape[1], self.shape[0])[self.pax] - 1
+                pres = [0.5 * drive * L, -0.5 * drive * L]
+        elif drive_dir is not None:
             f[drive_dir] = drive
         P = _Params(Re, c2, dt if dt is not None else default_dt(Re, c2), (C.c_double * 3)(*f),
-                    None, int(transposed))
+                    None, int(transposed), (C.c_double * 2)(*pres))
         if alpha is not None:
             a = np.ascontiguousarray(alpha, dtype=np.float64).reshape(-1)
             assert a.size == self.N
@@ -199,6 +217,18 @@ class Domain:
         """q_d = (1/N) sum u_d: superficial velocity (Fig. perm_computation)."""
         q = np.zeros(3)
         self._L.or_mean_velocity(self._ctx, _dptr(np.ascontiguousarray(U, dtype=np.float64)), _dptr(q))
+        return q
+
+    def superficial(self, q):
+        """Superficial velocity from the cell means q = (1/N) sum u.  Periodic domains:
+        q itself.  Fixed-pressure axis a: the flow crosses the n_a - 1 face planes between
+        the layers (q_a n_a / (n_a - 1)); the cross components live in the n_a - 2
+        interior layers (q_b n_a / (n_a - 2))."""
+        q = np.asarray(q, dtype=np.float64).copy()
+        if self.pax is not None:
+            n = (self.shape[2], self.shape[1], self.shape[0])[self.pax]
+            for d in range(3):
+                q[d] *= n / (n - 1) if d == self.pax else n / (n - 2)
         return q
 
     def percolation(self):
@@ -244,6 +274,8 @@ def ktensor(mask, dirs=(0, 1, 2), bc=(PERIODIC, PERIODIC, PERIODIC), tol=1e-10, 
     (k_sym, k_raw, runs)."""
     dom = dom or Domain(mask, bc)
     perc = dom.percolation()
+    if dom.pax is not None:
+        dirs = (dom.pax,)  # a fixed-pressure domain is driven along its pressure axis only
     Q = np.zeros((3, 3))
     runs = {}
     for j in dirs:
@@ -251,7 +283,7 @@ def ktensor(mask, dirs=(0, 1, 2), bc=(PERIODIC, PERIODIC, PERIODIC), tol=1e-10, 
             runs[j] = None
             continue
         r = dom.solve(j, tol=tol, check_every=check_every, max_iter=max_iter, alpha=alpha)
-        Q[:, j] = r["q"]
+        Q[:, j] = dom.superficial(r["q"])
         runs[j] = r
     k_raw = permeability_from_q(Q, dx=dx)
     return symmetrise(k_raw), k_raw, runs

@@ -37,6 +37,14 @@
  *   - optional per-cell drag alpha (not in the paper; alpha = 0 is the paper): the
  *     momentum residual gains -(1/Re) * alpha_f * u with alpha_f = (alpha(c) +
  *     alpha(c+e_d)) / 2 on the face.
+ *   - fixed-pressure inlet/outlet (Sec. 4 names a fixed pressure in the main flow
+ *     direction only in words; one axis a at most): the first and the last cell layer
+ *     along a are pressure reservoirs.  Their pressures are fixed (p_in, p_out), they
+ *     hold no velocity across a (their u_b, b != a, are non-fluid), and outside the box
+ *     along a counts as solid.  The n_a - 1 face planes u_a(0) .. u_a(n_a - 2) between
+ *     the layers carry the flow; at the inlet face u_a(0) and the outlet face
+ *     u_a(n_a - 2) the missing axial neighbour takes the face's own value (zero
+ *     gradient).  No body force: the drive h gives p_in - p_out = h (n_a - 1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,12 +56,14 @@
 
 #define OR_PERIODIC 0
 #define OR_WALL 1
+#define OR_PRESSURE 2
 #define OR_MAXOFF 4 /* neighbour offsets -4..4 are tabulated per axis */
 
 typedef struct {
     int64_t n[3];          /* nx, ny, nz; x fastest */
     int64_t N;
     int32_t bc[3];
+    int pax;               /* fixed-pressure axis, -1 if none */
     uint8_t *solid;        /* copy of the input mask */
     uint8_t *cell_fluid;   /* [N] */
     uint8_t *node_fluid;   /* [3][N] */
@@ -68,6 +78,7 @@ typedef struct {
     double f[3];           /* body force on the d-faces (the drive) */
     const double *alpha;   /* per-cell drag, may be NULL */
     int32_t transposed;    /* 1: use the transpose of the viscous operator (adjoint) */
+    double p_res[2];       /* fixed-pressure axis: reservoir pressures p_in, p_out */
 } or_params;
 
 /* ---------------------------------------------------------------- geometry */
@@ -99,6 +110,22 @@ static inline void or_coords(const or_ctx *g, int64_t c, int64_t *x, int64_t *y,
     int64_t r = c / g->n[0];
     *y = r % g->n[1];
     *z = r / g->n[1];
+}
+
+/* Layer of cell (x,y,z) along the fixed-pressure axis: 0 = inlet reservoir, 1 = outlet
+ * reservoir, -1 = interior (or no such axis). */
+static inline int or_reservoir(const or_ctx *g, int64_t x, int64_t y, int64_t z) {
+    if (g->pax < 0) return -1;
+    const int64_t v = g->pax == 0 ? x : (g->pax == 1 ? y : z);
+    return v == 0 ? 0 : (v == g->n[g->pax] - 1 ? 1 : -1);
+}
+
+/* Pressure of cell c: the fixed reservoir value in a reservoir layer, else p[c]. */
+static inline double or_p(const or_ctx *g, const or_params *P, const double *p, int64_t c) {
+    int64_t x, y, z;
+    or_coords(g, c, &x, &y, &z);
+    const int r = or_reservoir(g, x, y, z);
+    return r < 0 ? p[c] : P->p_res[r];
 }
 
 /* Appendix B / Fig. neighborhoodCases: case of a fluid node from the fluid flags of
@@ -144,7 +171,11 @@ or_ctx *or_ctx_create(int64_t nx, int64_t ny, int64_t nz, const int32_t bc[3], c
     if (!g) return NULL;
     g->n[0] = nx; g->n[1] = ny; g->n[2] = nz;
     g->N = nx * ny * nz;
-    for (int a = 0; a < 3; ++a) g->bc[a] = bc[a];
+    g->pax = -1;
+    for (int a = 0; a < 3; ++a) {
+        g->bc[a] = bc[a];
+        if (bc[a] == OR_PRESSURE && g->pax < 0) g->pax = a;
+    }
     int64_t N = g->N;
     g->solid = (uint8_t *)malloc((size_t)N);
     g->cell_fluid = (uint8_t *)malloc((size_t)N);
@@ -171,9 +202,11 @@ or_ctx *or_ctx_create(int64_t nx, int64_t ny, int64_t nz, const int32_t bc[3], c
     for (int64_t c = 0; c < N; ++c) {
         int64_t x, y, z;
         or_coords(g, c, &x, &y, &z);
+        const int res = or_reservoir(g, x, y, z);
         for (int d = 0; d < 3; ++d) {
             int64_t cp = or_nb(g, x, y, z, d, +1);
             g->node_fluid[d * N + c] = (g->cell_fluid[c] && cp >= 0 && g->cell_fluid[cp]) ? 1 : 0;
+            if (res >= 0 && d != g->pax) g->node_fluid[d * N + c] = 0;  /* reservoirs carry no cross flow */
         }
     }
     #pragma omp parallel for schedule(static)
@@ -233,7 +266,14 @@ void or_momentum_residual(const or_ctx *g, const or_params *P, const double *U, 
                     const int64_t cm = or_nb(g, x, y, z, d, -1);
                     /* along the flow direction: 3-point second difference; a non-fluid
                      * neighbour (or one outside a wall) contributes 0 */
-                    double lap = (nf[cp] ? Ud[cp] : 0.0) - 2.0 * u0 + ((cm >= 0 && nf[cm]) ? Ud[cm] : 0.0);
+                    double up = (cp >= 0 && nf[cp]) ? Ud[cp] : 0.0, um = (cm >= 0 && nf[cm]) ? Ud[cm] : 0.0;
+                    if (d == g->pax) {
+                        /* inlet / outlet face: zero-gradient axial neighbour */
+                        const int64_t v = d == 0 ? x : (d == 1 ? y : z);
+                        if (v == 0) um = u0;
+                        if (v == g->n[d] - 2) up = u0;
+                    }
+                    double lap = up - 2.0 * u0 + um;
                     for (int i = 0; i < 3; ++i) {
                         if (i == d) continue;
                         if (!P->transposed) {
@@ -251,7 +291,7 @@ void or_momentum_residual(const or_ctx *g, const or_params *P, const double *U, 
                         }
                     }
                     if (P->alpha) lap -= 0.5 * (P->alpha[c] + P->alpha[cp]) * u0;
-                    Rd[c] = inv_re * lap - (p[cp] - p[c]) + P->f[d];
+                    Rd[c] = inv_re * lap - (or_p(g, P, p, cp) - or_p(g, P, p, c)) + P->f[d];
                 }
     }
 }
@@ -264,7 +304,7 @@ void or_divergence(const or_ctx *g, const double *U, double *div) {
         for (int64_t y = 0; y < ny; ++y)
             for (int64_t x = 0; x < nx; ++x) {
                 const int64_t c = or_index(g, x, y, z);
-                if (!g->cell_fluid[c]) { div[c] = 0.0; continue; }
+                if (!g->cell_fluid[c] || or_reservoir(g, x, y, z) >= 0) { div[c] = 0.0; continue; }
                 double s = 0.0;
                 for (int d = 0; d < 3; ++d) s += or_u(g, U, d, c) - or_u(g, U, d, or_nb(g, x, y, z, d, -1));
                 div[c] = s;
@@ -283,8 +323,11 @@ void or_iterate(const or_ctx *g, const or_params *P, double *U, double *p, int64
         for (int64_t k = 0; k < 3 * N; ++k) U[k] += P->dt * R[k];
         or_divergence(g, U, div);
         #pragma omp parallel for schedule(static)
-        for (int64_t c = 0; c < N; ++c)
-            if (g->cell_fluid[c]) p[c] -= P->dt * P->c2 * div[c];
+        for (int64_t c = 0; c < N; ++c) {
+            if (!g->cell_fluid[c]) continue;
+            /* reservoir cells keep their fixed pressure; div is 0 there */
+            p[c] = or_p(g, P, p, c) - P->dt * P->c2 * div[c];
+        }
     }
     free(R);
     free(div);
@@ -390,6 +433,35 @@ void or_percolation(const or_ctx *g, int32_t out[3]) {
                         for (int k = 0; k < 3; ++k)
                             if (w[k * N + b] != wn[k]) out[k] = 1;
                     }
+                }
+        }
+    }
+    if (g->pax >= 0) {
+        /* fixed-pressure axis: a path of pore cells from the inlet reservoir layer to the
+         * outlet one; reservoir cells carry no cross flow, so a path leaves a reservoir
+         * only along the axis */
+        const int a = g->pax;
+        out[a] = 0;
+        memset(vis, 0, (size_t)N);
+        int64_t head = 0, tail = 0;
+        for (int64_t c = 0; c < N; ++c) {
+            int64_t x, y, z;
+            or_coords(g, c, &x, &y, &z);
+            if (g->cell_fluid[c] && or_reservoir(g, x, y, z) == 0) { vis[c] = 1; queue[tail++] = c; }
+        }
+        while (head < tail && !out[a]) {
+            int64_t c = queue[head++];
+            int64_t co[3];
+            or_coords(g, c, &co[0], &co[1], &co[2]);
+            const int rc = or_reservoir(g, co[0], co[1], co[2]);
+            if (rc == 1) { out[a] = 1; break; }
+            for (int ax = 0; ax < 3; ++ax)
+                for (int m = -1; m <= 1; m += 2) {
+                    if (rc == 0 && ax != a) continue;
+                    int64_t b = or_nb(g, co[0], co[1], co[2], ax, m);
+                    if (b < 0 || !g->cell_fluid[b] || vis[b]) continue;
+                    vis[b] = 1;
+                    queue[tail++] = b;
                 }
         }
     }
