@@ -65,7 +65,20 @@ typedef enum pm_status {
     PM_ERR_TOO_LARGE = 10       /* domain exceeds pm_iterate_noalloc's fixed scratch */
 } pm_status;
 
-enum { PM_BC_PERIODIC = 0, PM_BC_WALL = 1 };
+/* Outer boundary per axis.
+ *   PM_BC_PERIODIC  the domain repeats (Sec. 4; the drive is a pressure jump across it)
+ *   PM_BC_WALL      no-slip wall: the cells outside the box count as solid
+ *   PM_BC_PRESSURE  fixed-pressure inlet/outlet (Sec. 4 names a fixed pressure in the main
+ *                   flow direction; this is the library's reading of it): the first and
+ *                   the last cell layer along the axis are reservoirs with fixed pressures
+ *                   p_in and p_out and no flow inside them (their velocities across the
+ *                   axis are 0); outside the box counts as solid; the inlet and outlet
+ *                   faces use a zero-gradient axial neighbour.  At most one axis, with at
+ *                   least 3 cells; the drive must be along it (p_in - p_out = drive x
+ *                   (n_axis - 1) dx).  Supported by pm_iterate and pm_solve_direction
+ *                   (PM_FP32_RED64 and PM_FP64); the other entry points return
+ *                   PM_ERR_UNSUPPORTED. */
+enum { PM_BC_PERIODIC = 0, PM_BC_WALL = 1, PM_BC_PRESSURE = 2 };
 
 /* Arithmetic of the pseudo-time sweeps. */
 enum {
@@ -81,7 +94,7 @@ typedef struct pm_domain {
     int32_t mask_on_device;   /* 1: mask is a device pointer */
     double voxel_size;        /* dx; k is returned in dx^2 units (m^2 if dx in m) */
     double viscosity;         /* mu; scales the returned velocities only */
-    int32_t bc[3];            /* per axis x, y, z: PM_BC_PERIODIC or PM_BC_WALL */
+    int32_t bc[3];            /* per axis x, y, z: PM_BC_PERIODIC, PM_BC_WALL or PM_BC_PRESSURE */
 } pm_domain;
 
 typedef struct pm_options {
@@ -146,6 +159,8 @@ PM_API double pm_time_step(const pm_options *opt);
  * f on the fluid faces normal to axis dir (iteration units, Sec. 4).
  *   u: device, 3*N values, p: device, N values; float for PM_FP32_*, double for PM_FP64.
  *   Values on non-fluid faces / solid cells are set to 0 on entry.
+ *   With a PM_BC_PRESSURE axis, dir must be that axis; drive sets p_in - p_out =
+ *   drive x (n_axis - 1) (no body force) and the reservoir cells of p hold p_in / p_out.
  *   Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA. */
 PM_API int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_options *opt, int64_t n,
                void *u, void *p, void *cuda_stream);
@@ -176,8 +191,12 @@ PM_API int pm_iterate_noalloc(const pm_domain *dom, int dir, double drive, const
  *   u0 / p0 (device, same layout and units as u / p): warm start, or NULL for zero.
  *   k_col (host, 3 doubles, may be NULL): column dir of k (Appendix C), dx^2 units.
  *   st (host, may be NULL): statistics.
+ *   With a PM_BC_PRESSURE axis (dir must be that axis): the superficial velocities are the
+ *   mean flux per face plane between the layers (q_dir n / (n - 1)) and the mean of the
+ *   cross components over the n - 2 interior layers (q_i n / (n - 2)); p includes the
+ *   fixed reservoir pressures.  PM_FP32_DC64 is not supported there (PM_ERR_UNSUPPORTED).
  *   Errors: PM_ERR_INVALID_ARG, PM_ERR_NO_FLUID, PM_ERR_NOT_PERCOLATING (k_col = 0),
- *   PM_ERR_NOT_CONVERGED, PM_ERR_DIVERGED, PM_ERR_OOM, PM_ERR_CUDA. */
+ *   PM_ERR_NOT_CONVERGED, PM_ERR_DIVERGED, PM_ERR_UNSUPPORTED, PM_ERR_OOM, PM_ERR_CUDA. */
 PM_API int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_options *opt,
                        float *u, float *p, const float *u0, const float *p0, double *k_col,
                        pm_stats *st, void *cuda_stream);

@@ -28,6 +28,7 @@ PM_ERR_TOO_LARGE = 10
 
 PERIODIC = 0
 WALL = 1
+PRESSURE = 2  # fixed-pressure inlet/outlet reservoirs: first and last layer along the axis
 
 FP32_RED64 = 0
 FP32_DC64 = 1

@@ -116,16 +116,31 @@ int launch_grid(long long n) {
 struct Geometry {
     int nx = 0, ny = 0, nz = 0;
     int per[3] = {1, 1, 1};
+    int pax = -1;               // fixed-pressure axis, -1 if none
     long long N = 0;
     uint8_t *flags = nullptr;   // device, one byte per cell (simple kernel)
     uint32_t *code = nullptr;   // device, one stencil code word per cell (tiled kernel)
 };
 
+// Fixed-pressure axis of a domain, -1 if none.
+int pressure_axis(const pm_domain *dom) {
+    for (int a = 0; a < 3; ++a)
+        if (dom->bc[a] == PM_BC_PRESSURE) return a;
+    return -1;
+}
+
 int validate_domain(const pm_domain *dom) {
     if (!dom || !dom->mask) return PM_ERR_INVALID_ARG;
     if (dom->nx < 1 || dom->ny < 1 || dom->nz < 1) return PM_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (dom->bc[a] != PM_BC_PERIODIC && dom->bc[a] != PM_BC_WALL) return PM_ERR_INVALID_ARG;
+    int npres = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (dom->bc[a] != PM_BC_PERIODIC && dom->bc[a] != PM_BC_WALL && dom->bc[a] != PM_BC_PRESSURE)
+            return PM_ERR_INVALID_ARG;
+        if (dom->bc[a] == PM_BC_PRESSURE) {
+            const int n = a == 0 ? dom->nx : (a == 1 ? dom->ny : dom->nz);
+            if (++npres > 1 || n < 3) return PM_ERR_INVALID_ARG;  // one axis, two reservoirs + 1 layer
+        }
+    }
     if (!(dom->voxel_size > 0) || !(dom->viscosity > 0)) return PM_ERR_INVALID_ARG;
     return PM_OK;
 }
@@ -156,6 +171,7 @@ int build_geometry(const pm_domain *dom, cudaStream_t s, Scratch &scr, Geometry 
     g.ny = dom->ny;
     g.nz = dom->nz;
     for (int a = 0; a < 3; ++a) g.per[a] = dom->bc[a] == PM_BC_PERIODIC;
+    g.pax = pressure_axis(dom);
     g.N = (long long)g.nx * g.ny * g.nz;
     int st = scr.alloc(&g.flags, (size_t)g.N);
     if (st) return st;
@@ -167,7 +183,7 @@ int build_geometry(const pm_domain *dom, cudaStream_t s, Scratch &scr, Geometry 
         dmask = m;
     }
     classify_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
-                                                     g.flags);
+                                                     g.pax, g.flags);
     PM_CK(cudaGetLastError());
     if ((st = scr.alloc(&g.code, (size_t)g.N))) return st;
     code_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.code);
@@ -179,6 +195,45 @@ int build_geometry(const pm_domain *dom, cudaStream_t s, Scratch &scr, Geometry 
 // Breadth-first search that carries, per visited cell, how often the path to it crossed
 // each periodic boundary; meeting a visited cell with another crossing count along
 // axis a closes a loop that wraps around a.
+// Fixed-pressure axis a: is there a path of pore cells from the inlet reservoir layer to
+// the outlet one?  Reservoir cells carry no flow across the axis, so a path leaves a
+// reservoir only along a.
+int percolation_pressure(const std::vector<uint8_t> &mask, int nx, int ny, int nz, const int per[3], int a) {
+    const long long N = (long long)nx * ny * nz;
+    const int n[3] = {nx, ny, nz};
+    std::vector<uint8_t> seen((size_t)N, 0);
+    std::vector<long long> queue;
+    auto coord = [&](long long c, int ax) {
+        return ax == 0 ? (int)(c % nx) : (ax == 1 ? (int)((c / nx) % ny) : (int)(c / ((long long)nx * ny)));
+    };
+    for (long long c = 0; c < N; ++c)
+        if (!mask[c] && coord(c, a) == 0) {
+            seen[c] = 1;
+            queue.push_back(c);
+        }
+    for (size_t h = 0; h < queue.size(); ++h) {
+        const long long c = queue[h];
+        const int co[3] = {coord(c, 0), coord(c, 1), coord(c, 2)};
+        if (co[a] == n[a] - 1) return 1;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (co[a] == 0 && ax != a) continue;
+            for (int m = -1; m <= 1; m += 2) {
+                int cc[3] = {co[0], co[1], co[2]};
+                cc[ax] += m;
+                if (cc[ax] < 0 || cc[ax] >= n[ax]) {
+                    if (!per[ax]) continue;
+                    cc[ax] = (cc[ax] + n[ax]) % n[ax];
+                }
+                const long long b = cc[0] + (long long)nx * (cc[1] + (long long)ny * cc[2]);
+                if (mask[b] || seen[b]) continue;
+                seen[b] = 1;
+                queue.push_back(b);
+            }
+        }
+    }
+    return 0;
+}
+
 void percolation_host(const std::vector<uint8_t> &mask, int nx, int ny, int nz, const int per[3],
                       int out[3]) {
     const long long N = (long long)nx * ny * nz;
@@ -361,7 +416,13 @@ struct Solver {
             P.uout = F[k].u[1 - F[k].cur];
             P.pout = F[k].p[1 - F[k].cur];
             P.src = src[k];
-            for (int d = 0; d < 3; ++d) P.f[d] = (T)(d == dir[k] ? force[k] : 0.0);
+            for (int d = 0; d < 3; ++d) P.f[d] = (T)(d == dir[k] && g.pax < 0 ? force[k] : 0.0);
+            if (g.pax >= 0) {
+                // fixed-pressure drive: p_in - p_out = force x (n - 1), centred on 0
+                const int n = g.pax == 0 ? g.nx : (g.pax == 1 ? g.ny : g.nz);
+                P.pres[0] = (T)(0.5 * force[k] * (n - 1));
+                P.pres[1] = (T)(-0.5 * force[k] * (n - 1));
+            }
             const Geometry &q = G(k);
             P.code = q.code;
             P.nx = q.nx;
@@ -378,6 +439,7 @@ struct Solver {
         }
         B.multi = multi ? 1 : 0;
         B.active = multi ? active : nullptr;
+        B.pres_axis = g.pax + 1;
         return B;
     }
 
@@ -393,7 +455,7 @@ struct Solver {
 
     bool use_tiled() const {
         if (multi) return true;  // batches are built only from tiled-kernel shapes
-        return o.kernel == 0 && !transposed && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
+        return o.kernel == 0 && !transposed && g.pax < 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
     }
 
     // One sweep of the given mode; flips the ping-pong buffers.
@@ -837,7 +899,12 @@ int tensor_like(const pm_domain *dom, const pm_options *o, int ndirs, const int 
     if (!count_fluid(hm)) return PM_ERR_NO_FLUID;
     int per[3] = {dom->bc[0] == PM_BC_PERIODIC, dom->bc[1] == PM_BC_PERIODIC, dom->bc[2] == PM_BC_PERIODIC};
     int perc[3] = {1, 1, 1};
-    if (o->check_percolation) percolation_host(hm, dom->nx, dom->ny, dom->nz, per, perc);
+    const int pax = pressure_axis(dom);
+    if (pax >= 0 && o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
+    if (o->check_percolation) {
+        percolation_host(hm, dom->nx, dom->ny, dom->nz, per, perc);
+        if (pax >= 0) perc[pax] = percolation_pressure(hm, dom->nx, dom->ny, dom->nz, per, pax);
+    }
     int dirs[3], np = 0, slot[3] = {-1, -1, -1};
     bool blocked = false;
     for (int k = 0; k < ndirs; ++k) {
@@ -911,8 +978,17 @@ int tensor_like(const pm_domain *dom, const pm_options *o, int ndirs, const int 
     for (int k = 0; k < ndirs; ++k) {
         if (slot[k] < 0) continue;
         const pm_stats &b = bst[slot[k]];
-        // Appendix C: k_ij = mu q_i^(j) / h_j; iteration units mu = 1/Re, h = 1 -> q / Re
-        for (int i = 0; i < 3; ++i) kcols[k][i] = b.q[i] / o->Re * dom->voxel_size * dom->voxel_size;
+        // Appendix C: k_ij = mu q_i^(j) / h_j; iteration units mu = 1/Re, h = 1 -> q / Re.
+        // Fixed-pressure axis a (n cells): the flow crosses the n - 1 face planes between
+        // the layers, the cross components live in the n - 2 interior layers.
+        for (int i = 0; i < 3; ++i) {
+            double sup = 1.0;
+            if (pax >= 0) {
+                const double n = pax == 0 ? dom->nx : (pax == 1 ? dom->ny : dom->nz);
+                sup = i == pax ? n / (n - 1.0) : n / (n - 2.0);
+            }
+            kcols[k][i] = sup * b.q[i] / o->Re * dom->voxel_size * dom->voxel_size;
+        }
         if (st) {
             int perc_k = st[k].percolates;
             st[k] = b;
@@ -972,7 +1048,8 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
     const int per[3] = {dom->bc[0] == PM_BC_PERIODIC, dom->bc[1] == PM_BC_PERIODIC, dom->bc[2] == PM_BC_PERIODIC};
     PM_CK(cudaMemcpyAsync(mask, dom->mask, (size_t)N, dom->mask_on_device ? cudaMemcpyDeviceToDevice
                                                                           : cudaMemcpyHostToDevice, s));
-    classify_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], flags);
+    classify_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], -1,
+                                                   flags);
     code_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], code);
     sanitize_kernel<T><<<launch_grid(N), 256, 0, s>>>(flags, N, u, p);
     PM_CK(cudaGetLastError());
@@ -1234,6 +1311,7 @@ int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_options *o,
     if ((st = validate_options(o))) return st;
     if (dir < 0 || dir > 2 || !u || !p || n < 0) return PM_ERR_INVALID_ARG;
     if (o->precision == PM_FP32_DC64) return PM_ERR_INVALID_ARG;
+    if (pressure_axis(dom) >= 0 && dir != pressure_axis(dom)) return PM_ERR_INVALID_ARG;
     StreamScope ss(cuda_stream);
     if (ss.status) return ss.status;
     {
@@ -1255,6 +1333,7 @@ int pm_iterate_noalloc(const pm_domain *dom, int dir, double drive, const pm_opt
     if ((st = validate_options(o))) return st;
     if (dir < 0 || dir > 2 || !u || !p || n < 0) return PM_ERR_INVALID_ARG;
     if (o->precision == PM_FP32_DC64) return PM_ERR_INVALID_ARG;
+    if (pressure_axis(dom) >= 0) return PM_ERR_UNSUPPORTED;
     if ((long long)dom->nx * dom->ny * dom->nz > kNoAllocMaxCells) return PM_ERR_TOO_LARGE;
     unsigned char *scr = nullptr;
     if ((st = noalloc_scratch(&scr))) return st;
@@ -1275,6 +1354,7 @@ int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_opt
     if (rc) return rc;
     if ((rc = validate_options(o))) return rc;
     if (dir < 0 || dir > 2 || !(drive > 0)) return PM_ERR_INVALID_ARG;
+    if (pressure_axis(dom) >= 0 && dir != pressure_axis(dom)) return PM_ERR_INVALID_ARG;
     double kc[3][3];
     pm_stats local;
     int dirs[1] = {dir};
@@ -1293,7 +1373,7 @@ int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], 
     if (rc) return rc;
     if ((rc = validate_options(o))) return rc;
     if (dJ_dalpha && !w) return PM_ERR_INVALID_ARG;
-    if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
+    if (o->precision == PM_FP32_DC64 || pressure_axis(dom) >= 0) return PM_ERR_UNSUPPORTED;
     const double t0 = now_s();
     std::vector<uint8_t> hm;
     if ((rc = host_mask(dom, hm))) return rc;
@@ -1320,7 +1400,7 @@ int pm_batch_ktensor(int n_domains, const pm_domain *doms, const int32_t *drives
     if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
     for (int d = 0; d < n_domains; ++d) {
         if ((rc = validate_domain(&doms[d]))) return rc;
-        if (doms[d].nx % 4 != 0) return PM_ERR_UNSUPPORTED;
+        if (doms[d].nx % 4 != 0 || pressure_axis(&doms[d]) >= 0) return PM_ERR_UNSUPPORTED;
         for (int a = 0; a < 3; ++a)
             if (doms[d].bc[a] != doms[0].bc[a]) return PM_ERR_UNSUPPORTED;
         if (drives && (drives[d] < 0 || drives[d] > 7)) return PM_ERR_INVALID_ARG;
@@ -1346,6 +1426,7 @@ int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_options 
     if (rc) return rc;
     if ((rc = validate_options(o))) return rc;
     if (!k_out || !(drive > 0)) return PM_ERR_INVALID_ARG;
+    if (pressure_axis(dom) >= 0) return PM_ERR_UNSUPPORTED;  // one drive only: pm_solve_direction
     double kc[3][3];
     int dirs[3] = {0, 1, 2};
     if (o->precision == PM_FP64)

@@ -56,6 +56,7 @@ struct SweepProblem {
     T *pout;         // N
     const T *src;    // 4N source (r_u x3, r_p) or nullptr
     T f[3];          // body force per face direction (the drive)
+    T pres[2];       // fixed-pressure axis: inlet and outlet reservoir pressures
     double *partials;  // [nblocks][4] block sums (q_x, q_y, q_z, |div|^2) or nullptr
     // geometry of this problem (multi-geometry batches; otherwise equal to the batch's)
     const uint32_t *code;
@@ -81,6 +82,7 @@ struct SweepBatch {
     int nprob;
     int multi;             // 1: problems have their own geometry (tiled kernel, one unit per CTA)
     const int *active;     // device, per problem, 0 = skip (converged); nullptr = all active
+    int pres_axis;         // fixed-pressure axis + 1 (reservoir layers 0 and n - 1); 0 = none
     SweepProblem<T> prob[kMaxBatch];
 };
 

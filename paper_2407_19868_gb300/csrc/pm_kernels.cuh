@@ -9,9 +9,10 @@ namespace pmgb {
 // ------------------------------------------------------------------ neighbourhood
 // Algorithm 1 "Evaluate neighborhood": per cell the pore flag and the fluid flags of its
 // three +d face nodes (Sec. 4: a face between two pore cells carries flow; every face
-// touching solid is a no-slip / no-penetration face).
+// touching solid is a no-slip / no-penetration face).  pax >= 0: fixed-pressure axis,
+// whose first and last layers are reservoirs without flow across the axis.
 __global__ void classify_kernel(const uint8_t *__restrict__ mask, int nx, int ny, int nz, int px,
-                                int py, int pz, uint8_t *__restrict__ flags) {
+                                int py, int pz, int pax, uint8_t *__restrict__ flags) {
     long long N = (long long)nx * ny * nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
@@ -26,6 +27,10 @@ __global__ void classify_kernel(const uint8_t *__restrict__ mask, int nx, int ny
             if (xp >= 0 && !mask[xp + (long long)nx * (y + (long long)ny * z)]) f |= node_bit(0);
             if (yp >= 0 && !mask[x + (long long)nx * (yp + (long long)ny * z)]) f |= node_bit(1);
             if (zp >= 0 && !mask[x + (long long)nx * (y + (long long)ny * zp)]) f |= node_bit(2);
+            if (pax >= 0) {
+                const int v = pax == 0 ? x : (pax == 1 ? y : z), n = pax == 0 ? nx : (pax == 1 ? ny : nz);
+                if (v == 0 || v == n - 1) f &= (uint8_t)(kFlagCell | node_bit(pax));
+            }
         }
         flags[c] = f;
     }
@@ -112,11 +117,21 @@ __global__ void __launch_bounds__(256) sweep_simple_kernel(const SweepBatch<T> B
         if (xx < 0 || yy < 0 || zz < 0) return false;
         return (fl[lin(xx, yy, zz)] & node_bit(d)) != 0;
     };
-    // p^n at a cell (MODE kModeU: p^n is the input)
+    // fixed-pressure axis: 0 = inlet reservoir layer, 1 = outlet reservoir layer, -1 otherwise
+    const int pax = B.pres_axis - 1;
+    const int npax = pax == 0 ? nx : (pax == 1 ? ny : nz);
+    auto reservoir = [&](int xx, int yy, int zz) -> int {
+        if (pax < 0) return -1;
+        const int v = pax == 0 ? xx : (pax == 1 ? yy : zz);
+        return v == 0 ? 0 : (v == npax - 1 ? 1 : -1);
+    };
+    // p^n at a cell (MODE kModeU: p^n is the input); reservoirs hold their fixed pressure
     T div_own = T(0);
     auto pn = [&](int xx, int yy, int zz, bool own) -> T {
         long long c = lin(xx, yy, zz);
         if (!(fl[c] & kFlagCell)) return T(0);
+        const int res = reservoir(xx, yy, zz);
+        if (res >= 0) return P.pres[res];
         T p0 = P.pin[c];
         if (MODE == kModeU) return p0;
         int xm = nb_coord(xx - 1, nx, B.per[0]), ym = nb_coord(yy - 1, ny, B.per[1]),
@@ -145,10 +160,17 @@ __global__ void __launch_bounds__(256) sweep_simple_kernel(const SweepBatch<T> B
                 if (f0 & node_bit(d)) {
                     const T u0 = P.uin[d * N + c];
                     T lap;
-                    // along the flow direction: 3-point, non-fluid neighbours are 0
-                    if (d == 0) lap = U(0, xp1, y, z) - T(2) * u0 + U(0, xm1, y, z);
-                    else if (d == 1) lap = U(1, x, yp1, z) - T(2) * u0 + U(1, x, ym1, z);
-                    else lap = U(2, x, y, zp1) - T(2) * u0 + U(2, x, y, zm1);
+                    // along the flow direction: 3-point, non-fluid neighbours are 0; the
+                    // inlet / outlet face of a fixed-pressure axis has a zero-gradient
+                    // neighbour outside
+                    T up = d == 0 ? U(0, xp1, y, z) : (d == 1 ? U(1, x, yp1, z) : U(2, x, y, zp1));
+                    T um = d == 0 ? U(0, xm1, y, z) : (d == 1 ? U(1, x, ym1, z) : U(2, x, y, zm1));
+                    if (d == pax) {
+                        const int v = d == 0 ? x : (d == 1 ? y : z);
+                        if (v == 0) um = u0;
+                        if (v == npax - 2) up = u0;
+                    }
+                    lap = up - T(2) * u0 + um;
                     if (!TR) {
                         if (d != 0)
                             lap += perp_d2(u0, U(d, xm2, y, z), U(d, xm1, y, z), U(d, xp1, y, z), U(d, xp2, y, z),

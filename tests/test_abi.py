@@ -86,3 +86,40 @@ def test_struct_layout_matches_header(lib, tmp_path):
         assert int(out[st]) == C.sizeof(cls), st
         for f in fs:
             assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+
+
+def test_fixed_pressure_axis_rejections_before_any_device_work(lib):
+    """A fixed-pressure axis: one at most, at least 3 cells, drive along it; entry points
+    that need several drives or the transposed operator refuse it."""
+    L = lib.load()
+    o = lib.options()
+    mask = np.zeros((4, 4, 5), dtype=np.uint8)
+    k = (C.c_double * 9)()
+    kc = (C.c_double * 3)()
+
+    def dom(bc, m=mask):
+        nz, ny, nx = m.shape
+        return lib.Domain(nx, ny, nz, m.ctypes.data, 0, 1.0, 1.0, (C.c_int32 * 3)(*bc))
+
+    P = lib.PRESSURE
+    two = dom((P, P, 0))
+    assert L.pm_solve_direction(C.byref(two), 0, 1.0, C.byref(o), None, None, None, None, kc, None,
+                                None) == lib.PM_ERR_INVALID_ARG
+    short = dom((0, 0, P), np.zeros((2, 4, 5), dtype=np.uint8))
+    assert L.pm_solve_direction(C.byref(short), 2, 1.0, C.byref(o), None, None, None, None, kc, None,
+                                None) == lib.PM_ERR_INVALID_ARG
+    px = dom((P, 0, 1))
+    assert L.pm_solve_direction(C.byref(px), 1, 1.0, C.byref(o), None, None, None, None, kc, None,
+                                None) == lib.PM_ERR_INVALID_ARG
+    u = (C.c_float * (3 * mask.size))()
+    p = (C.c_float * mask.size)()
+    assert L.pm_iterate(C.byref(px), 2, 1.0, C.byref(o), 1, u, p, None) == lib.PM_ERR_INVALID_ARG
+    assert L.pm_permeability_tensor(C.byref(px), 1.0, C.byref(o), k, None, None, None) == lib.PM_ERR_UNSUPPORTED
+    assert L.pm_iterate_noalloc(C.byref(px), 0, 1.0, C.byref(o), 1, u, p, None) == lib.PM_ERR_UNSUPPORTED
+    w = (C.c_double * 9)(*([1.0] + [0.0] * 8))
+    assert L.pm_sensitivity(C.byref(px), None, w, C.byref(o), None, None, None, None) == lib.PM_ERR_UNSUPPORTED
+    doms = (lib.Domain * 1)(px)
+    assert L.pm_batch_ktensor(1, doms, None, C.byref(o), k, None, None, None) == lib.PM_ERR_UNSUPPORTED
+    dc = lib.options(precision="dc64")
+    assert L.pm_solve_direction(C.byref(px), 0, 1.0, C.byref(dc), None, None, None, None, kc, None,
+                                None) == lib.PM_ERR_UNSUPPORTED
