@@ -2,7 +2,7 @@
 //
 // A CTA owns a TX x TY column tile of the (x, y) plane and marches along z over a chunk
 // of planes.  Each plane of the five input arrays (u_x, u_y, u_z, p, stencil code) is
-// copied with its 2-voxel halo into a 4-stage shared-memory ring by cp.async, one plane
+// copied with its 2-voxel halo into a 5-stage shared-memory ring by cp.async, two planes
 // ahead of use, so each field value comes from DRAM once per sweep and the neighbour
 // reuse is served by shared memory (x, y) and per-thread register queues (z).
 //
@@ -93,16 +93,16 @@ __device__ __forceinline__ void cp_async_wait() {
 // (x0 + 2 lane + 1, y0 + ty).  Shared-memory boxes are BX = TX + 8 wide (x0 - 4 ..
 // x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4 high (y0 - 2 .. y0 + TY + 1); the
 // stencil needs +-2 in x and y.
-constexpr int kTX = 64, kTY = 8, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY;
+constexpr int kTX = 64, kTY = 12, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY;
 // Ring of kStages planes: planes t-2, t-1, t are read in step t while the copies of the
 // next kAhead planes are in flight.
-constexpr int kStages = 4, kAhead = kStages - 3;
+constexpr int kStages = 5, kAhead = kStages - 3;
 // p^n, the input pressure and the stencil codes are needed on box rows 2 .. kTY + 2 (tile
 // rows and the +y halo row) only, u_y on rows 1 .. kTY + 2; u_x and u_z on all rows
 constexpr int kPNL = (kTY + 1) * kBX, kPNo = 2 * kBX;
 constexpr int kUYL = (kTY + 2) * kBX, kUYo = kBX;
 // CTAs per SM the FP32 kernel is built for (registers and shared memory)
-constexpr int kMinBlocks = 3;
+constexpr int kMinBlocks = 2;
 constexpr int kNT = (kTX / 2) * kTY;
 
 // One ring stage: the five arrays of one plane, contiguous, so that every access is a
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     }
     // halo p^n: the last warp takes the row y0 + TY (pairs), the last TY lanes of the
     // warp before it the column x0 + TX (single cells); for FP32 these lanes issue no
-    // copies (216 chunks per array), which balances the work before the barrier
+    // copies (288 chunks per array), which balances the work before the barrier
     const bool hrow = ty == kTY - 1, hcol = ty == kTY - 2 && lane >= 32 - kTY;
     const int hown = hrow ? (kTY + 2) * kBX + 4 + 2 * lane : (lane - (32 - kTY) + 2) * kBX + kTX + 4;
     long long hg = -1;
