@@ -541,9 +541,27 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         // publish p^n of plane t-1 (own pair and halo cells) for the next step's update
         *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own - 2 * kBX]) = pn_new;
         if (hrow) {
-            T *dst = &S.pn[(t - 1) & 1][hown - 2 * kBX];
-            dst[0] = press1(G1, G2, hown, t - 1, hg);
-            dst[1] = press1(G1, G2, hown + 1, t - 1, hg >= 0 ? hg + 1 : -1);
+            // the +y halo row as pairs (same arithmetic as press1, 2-wide loads)
+            const Pair<uint32_t> hc = ld2u<T>(&G1.cd[hown - kPNo]);
+            const Pair<T> hp = ld2(&G1.pin[hown - kPNo]);
+            const Pair<T> hux = ld2(&G1.ux[hown]);
+            const T huxl = G1.ux[hown - 1];
+            const Pair<T> huy = ld2(&G1.uy[hown - kUYo]), huyd = ld2(&G1.uy[hown - kBX - kUYo]);
+            const Pair<T> huz = ld2(&G1.uz[hown]), huzd = ld2(&G2.uz[hown]);
+            const T dv0 = (hux.a - huxl) + (huy.a - huyd.a) + (huz.a - huzd.a);
+            const T dv1 = (hux.b - hux.a) + (huy.b - huyd.b) + (huz.b - huzd.b);
+            T rp0 = T(0), rp1 = T(0);
+            if (SRC && hg >= 0) {
+                const int gz = nb_coord(t - 1, nz, B.per[2]);
+                if (gz >= 0) {
+                    rp0 = P.src[3 * N + (long long)gz * plane + hg];
+                    rp1 = P.src[3 * N + (long long)gz * plane + hg + 1];
+                }
+            }
+            Pair<T> hn;
+            hn.a = (hc.a & 1u) ? (MODE == kModeU ? hp.a : hp.a - B.dtc2 * (dv0 - rp0)) : T(0);
+            hn.b = (hc.b & 1u) ? (MODE == kModeU ? hp.b : hp.b - B.dtc2 * (dv1 - rp1)) : T(0);
+            *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][hown - 2 * kBX]) = hn;
         } else if (hcol) {
             S.pn[(t - 1) & 1][hown - 2 * kBX] = press1(G1, G2, hown, t - 1, hg);
         }
