@@ -15,6 +15,8 @@
 // neighbours at all.
 #pragma once
 
+#include <type_traits>
+
 #include "pm_common.cuh"
 
 namespace pmgb {
@@ -81,6 +83,11 @@ __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, in
 __device__ __forceinline__ void cp_async16(void *s, const void *g) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+// zero-filling form: src_bytes = 0 reads nothing and writes 16 zero bytes
+__device__ __forceinline__ void cp_async16z(void *s, const void *g, unsigned src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(g), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -290,26 +297,18 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         for (int r = 0; r < FR; ++r) {
             if (!fhas[r]) continue;
             const int e = fs[r];
-            if (gz >= 0 && fo[r] >= 0) {
-                const long long o = po + fo[r];
-                cp_async16(&G.ux[e], gux + o);
-                cp_async16(&G.uz[e], guz + o);
-                if (fuy[r]) cp_async16(&G.uy[e - kUYo], guy + o);
-                if (fp[r]) cp_async16(&G.pin[e - kPNo], gp + o);
-            } else {
-#pragma unroll
-                for (int j = 0; j < FE; ++j) {
-                    G.ux[e + j] = T(0);
-                    G.uz[e + j] = T(0);
-                    if (fuy[r]) G.uy[e - kUYo + j] = T(0);
-                    if (fp[r]) G.pin[e - kPNo + j] = T(0);
-                }
-            }
+            // outside a wall: the zero-filling copy reads nothing (a valid address is given)
+            const bool in = gz >= 0 && fo[r] >= 0;
+            const long long o = in ? po + fo[r] : 0;
+            const unsigned nb = in ? 16u : 0u;
+            cp_async16z(&G.ux[e], gux + o, nb);
+            cp_async16z(&G.uz[e], guz + o, nb);
+            if (fuy[r]) cp_async16z(&G.uy[e - kUYo], guy + o, nb);
+            if (fp[r]) cp_async16z(&G.pin[e - kPNo], gp + o, nb);
         }
         if (chas) {
-            if (gz >= 0 && co >= 0) cp_async16(&G.cd[cs], code + po + co);
-            else
-                for (int j = 0; j < 4; ++j) G.cd[cs + j] = 0u;
+            const bool in = gz >= 0 && co >= 0;
+            cp_async16z(&G.cd[cs], code + (in ? po + co : 0), in ? 16u : 0u);
         }
         cp_async_commit();
     };
@@ -341,11 +340,11 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     const long long ex1_off = wxp >= 0 ? (long long)wxp - (gx_own + 1) : 0;  // second cell's +x
     const long long ey_off = wyp >= 0 ? ((long long)wyp - gy_own) * nx : 0;
 
-    Pair<T> qx[5], qy[5], qz[3];
+    Pair<T> qx[5], qy[5], qz[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) qx[i] = qy[i] = Pair<T>{T(0), T(0)};
 #pragma unroll
-    for (int i = 0; i < 3; ++i) qz[i] = Pair<T>{T(0), T(0)};
+    for (int i = 0; i < 5; ++i) qz[i] = Pair<T>{T(0), T(0)};
     Pair<T> pn_m{T(0), T(0)};  // own p^n on the plane being updated (m)
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 
@@ -383,7 +382,13 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
 
     T *outx = P.uout + (long long)m0 * plane + gin_own;
     T *outp = P.pout + (long long)m0 * plane + gin_own;
-    for (int t = t0; t <= m1 + 1; ++t) {
+    const int tend = m1 + 1;
+    // one plane step; kRot = step index mod 5.  The z queues are circular with compile-time
+    // slots, so advancing them moves no registers: after this step's load, queue entry k
+    // (u_x, u_y: planes m-2 .. m+2 of the updated plane m = t-2; u_z: planes m-1 .. m+1 as
+    // entries 0 .. 2) lives in slot (kRot + 1 + k) % 5.  The loop below unrolls five steps.
+    auto step = [&](auto Rc, int t) {
+        constexpr int kRot = decltype(Rc)::value;
         cp_async_wait<kAhead - 1>();
         __syncthreads();
         {
@@ -393,16 +398,9 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         }
         const TiledStage<T> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
         // z queues of the own column pair
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            qx[i] = qx[i + 1];
-            qy[i] = qy[i + 1];
-        }
-        qx[4] = ld2(&G0.ux[own]);
-        qy[4] = ld2(&G0.uy[own - kUYo]);
-        qz[0] = qz[1];
-        qz[1] = qz[2];
-        qz[2] = ld2(&G1.uz[own]);
+        qx[kRot % 5] = ld2(&G0.ux[own]);
+        qy[kRot % 5] = ld2(&G0.uy[own - kUYo]);
+        qz[(kRot + 3) % 5] = ld2(&G1.uz[own]);
         // own p^n on plane t-1 (kept in registers until after the update of plane t-2)
         Pair<T> pn_new;
         {
@@ -410,8 +408,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             const Pair<T> pin = ld2(&G1.pin[own - kPNo]);
             const Pair<T> uyd = ld2(&G1.uy[own - kBX - kUYo]);
             const T uxl = G1.ux[own - 1];
-            T dv0 = (qx[3].a - uxl) + (qy[3].a - uyd.a) + (qz[2].a - qz[1].a);
-            T dv1 = (qx[3].b - qx[3].a) + (qy[3].b - uyd.b) + (qz[2].b - qz[1].b);
+            T dv0 = (qx[(kRot + 1 + 3) % 5].a - uxl) + (qy[(kRot + 1 + 3) % 5].a - uyd.a) + (qz[(kRot + 1 + 2) % 5].a - qz[(kRot + 1 + 1) % 5].a);
+            T dv1 = (qx[(kRot + 1 + 3) % 5].b - qx[(kRot + 1 + 3) % 5].a) + (qy[(kRot + 1 + 3) % 5].b - uyd.b) + (qz[(kRot + 1 + 2) % 5].b - qz[(kRot + 1 + 1) % 5].b);
             T rp0 = T(0), rp1 = T(0);
             if (SRC && gin_wrap >= 0) {
                 const int gz = nb_coord(t - 1, nz, B.per[2]);
@@ -435,9 +433,9 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             // ------------------------------------------------------ update on plane m
             Pair<T> ux_n, uy_n, uz_n;
             if (MODE == kModeP) {
-                ux_n = qx[2];
-                uy_n = qy[2];
-                uz_n = qz[1];
+                ux_n = qx[(kRot + 1 + 2) % 5];
+                uy_n = qy[(kRot + 1 + 2) % 5];
+                uz_n = qz[(kRot + 1 + 1) % 5];
             } else {
                 const Pair<uint32_t> c = ld2u<T>(&G2.cd[own - kPNo]);
                 const T *PN = S.pn[m & 1];  // index: box index - 2 kBX
@@ -445,7 +443,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 const long long gidx = (long long)m * plane + gin_own;
                 // u_x: along x (box), across y (box) and z (queue)
                 {
-                    const Pair<T> u0 = qx[2];
+                    const Pair<T> u0 = qx[(kRot + 1 + 2) % 5];
                     const Pair<T> L = ld2(&ux[own - 2]), R = ld2(&ux[own + 2]);
                     const Pair<T> ym2 = ld2(&ux[own - 2 * kBX]), ym1 = ld2(&ux[own - kBX]);
                     const Pair<T> yp1 = ld2(&ux[own + kBX]), yp2 = ld2(&ux[own + 2 * kBX]);
@@ -453,8 +451,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                     T lap1 = fma(T(-2), u0.b, R.a + u0.a);
                     perp(lap0, c.a, code_shift(0, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
                     perp(lap1, c.b, code_shift(0, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
-                    perp(lap0, c.a, code_shift(0, 2), qx[0].a, qx[1].a, u0.a, qx[3].a, qx[4].a);
-                    perp(lap1, c.b, code_shift(0, 2), qx[0].b, qx[1].b, u0.b, qx[3].b, qx[4].b);
+                    perp(lap0, c.a, code_shift(0, 2), qx[(kRot + 1 + 0) % 5].a, qx[(kRot + 1 + 1) % 5].a, u0.a, qx[(kRot + 1 + 3) % 5].a, qx[(kRot + 1 + 4) % 5].a);
+                    perp(lap1, c.b, code_shift(0, 2), qx[(kRot + 1 + 0) % 5].b, qx[(kRot + 1 + 1) % 5].b, u0.b, qx[(kRot + 1 + 3) % 5].b, qx[(kRot + 1 + 4) % 5].b);
                     if (ALPHA) {
                         lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + 1]) * u0.a;
                         lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ex1_off]) * u0.b;
@@ -472,7 +470,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 }
                 // u_y: along y (box), across x (box) and z (queue)
                 {
-                    const Pair<T> u0 = qy[2];
+                    const Pair<T> u0 = qy[(kRot + 1 + 2) % 5];
                     const int oy = own - kUYo;
                     const Pair<T> L = ld2(&uy[oy - 2]), R = ld2(&uy[oy + 2]);
                     const Pair<T> ym1 = ld2(&uy[oy - kBX]), yp1 = ld2(&uy[oy + kBX]);
@@ -480,8 +478,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                     T lap1 = fma(T(-2), u0.b, yp1.b + ym1.b);
                     perp(lap0, c.a, code_shift(1, 0), L.a, L.b, u0.a, u0.b, R.a);
                     perp(lap1, c.b, code_shift(1, 0), L.b, u0.a, u0.b, R.a, R.b);
-                    perp(lap0, c.a, code_shift(1, 2), qy[0].a, qy[1].a, u0.a, qy[3].a, qy[4].a);
-                    perp(lap1, c.b, code_shift(1, 2), qy[0].b, qy[1].b, u0.b, qy[3].b, qy[4].b);
+                    perp(lap0, c.a, code_shift(1, 2), qy[(kRot + 1 + 0) % 5].a, qy[(kRot + 1 + 1) % 5].a, u0.a, qy[(kRot + 1 + 3) % 5].a, qy[(kRot + 1 + 4) % 5].a);
+                    perp(lap1, c.b, code_shift(1, 2), qy[(kRot + 1 + 0) % 5].b, qy[(kRot + 1 + 1) % 5].b, u0.b, qy[(kRot + 1 + 3) % 5].b, qy[(kRot + 1 + 4) % 5].b);
                     if (ALPHA) {
                         lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + ey_off]) * u0.a;
                         lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ey_off]) * u0.b;
@@ -499,12 +497,12 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 }
                 // u_z: along z (queue), across x and y (box)
                 {
-                    const Pair<T> u0 = qz[1];
+                    const Pair<T> u0 = qz[(kRot + 1 + 1) % 5];
                     const Pair<T> L = ld2(&uz[own - 2]), R = ld2(&uz[own + 2]);
                     const Pair<T> ym2 = ld2(&uz[own - 2 * kBX]), ym1 = ld2(&uz[own - kBX]);
                     const Pair<T> yp1 = ld2(&uz[own + kBX]), yp2 = ld2(&uz[own + 2 * kBX]);
-                    T lap0 = fma(T(-2), u0.a, qz[2].a + qz[0].a);
-                    T lap1 = fma(T(-2), u0.b, qz[2].b + qz[0].b);
+                    T lap0 = fma(T(-2), u0.a, qz[(kRot + 1 + 2) % 5].a + qz[(kRot + 1 + 0) % 5].a);
+                    T lap1 = fma(T(-2), u0.b, qz[(kRot + 1 + 2) % 5].b + qz[(kRot + 1 + 0) % 5].b);
                     perp(lap0, c.a, code_shift(2, 0), L.a, L.b, u0.a, u0.b, R.a);
                     perp(lap1, c.b, code_shift(2, 0), L.b, u0.a, u0.b, R.a, R.b);
                     perp(lap0, c.a, code_shift(2, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
@@ -569,6 +567,17 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         s2 = s1;
         s1 = s0;
         s0 = s0 == kStages - 1 ? 0 : s0 + 1;
+        };
+    for (int t = t0; t <= tend; t += 5) {
+        step(std::integral_constant<int, 0>{}, t);
+        if (t + 1 > tend) break;
+        step(std::integral_constant<int, 1>{}, t + 1);
+        if (t + 2 > tend) break;
+        step(std::integral_constant<int, 2>{}, t + 2);
+        if (t + 3 > tend) break;
+        step(std::integral_constant<int, 3>{}, t + 3);
+        if (t + 4 > tend) break;
+        step(std::integral_constant<int, 4>{}, t + 4);
     }
     // drain this column's copies before the ring is reused
     cp_async_wait<0>();
