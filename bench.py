@@ -354,7 +354,9 @@ def run_sequence(args):
             "generate_s": gen_s, "status": r["status"], "seconds_all_k": secs, "fluid_voxel_updates_per_s": upd / secs,
             "problems": sum(1 for d in range(len(doms)) for j in range(2) if r["stats"][d][j]["percolates"]),
             "iters": [[r["stats"][d][j]["iters"] for j in range(2)] for d in range(len(doms))],
-            "converged": [[r["stats"][d][j]["status"] == 0 for j in range(2)] for d in range(len(doms))],
+            "converged": [[r["stats"][d][j]["percolates"] and r["stats"][d][j]["status"] == 0 for j in range(2)]
+                          for d in range(len(doms))],
+            "percolates": [[bool(r["stats"][d][j]["percolates"]) for j in range(2)] for d in range(len(doms))],
             "delta": [[r["stats"][d][j]["delta"] for j in range(2)] for d in range(len(doms))],
             "max_iter": args.seq_max_iter,
             "sweep_ms": r["stats"][0][0]["sweep_ms"],
