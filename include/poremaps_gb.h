@@ -245,6 +245,22 @@ PM_API int pm_batch_ktensor(int n_domains, const pm_domain *doms, const int32_t 
 PM_API int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *opt,
                           float *dJ_dalpha, double *J, double k_raw[9], void *cuda_stream);
 
+/* Spectral form of a permeability tensor (Sec. 2, Eq. 3dK_eigen): principal permeabilities
+ * lambda (ascending) and principal axes, from the symmetric part of k (host only, no GPU).
+ *   k: host, 9 doubles, row-major.  lambda: host, 3 doubles out.
+ *   axes: host, 9 doubles out, or NULL; column j (axes[3*i + j], i = 0..2) is the unit
+ *   principal axis of lambda[j], signed so that its largest-magnitude component is positive
+ *   (the rotation tensor R of Sec. 2 up to the order and signs of its columns).
+ *   Cyclic Jacobi rotations to machine precision.
+ *   Errors: PM_ERR_INVALID_ARG (NULL or non-finite input). */
+PM_API int pm_principal_axes(const double k[9], double lambda[3], double axes[9]);
+
+/* Material class of Sec. 2 from the principal permeabilities: 0 isotropy (all three equal),
+ * 1 transverse anisotropy (exactly two equal), 2 orthotropy (all different); two values
+ * count as equal when they differ by at most rel_tol x the largest |lambda|.
+ * Returns the class, or -1 for NULL / non-finite input or rel_tol < 0. */
+PM_API int pm_anisotropy_class(const double lambda[3], double rel_tol);
+
 #ifdef __cplusplus
 }
 #endif

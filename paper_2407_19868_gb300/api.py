@@ -114,6 +114,8 @@ def load():
         L.pm_sensitivity.argtypes = [C.POINTER(Domain), vp, dp, C.POINTER(Options), vp, dp, dp, vp]
         L.pm_batch_ktensor.argtypes = [C.c_int, C.POINTER(Domain), C.POINTER(C.c_int32), C.POINTER(Options), dp, dp,
                                        C.POINTER(Stats), vp]
+        L.pm_principal_axes.argtypes = [dp, dp, dp]
+        L.pm_anisotropy_class.argtypes = [dp, C.c_double]
         _LIB = L
         return L
 
@@ -217,6 +219,28 @@ def solve_direction(mask, drive_dir: int, drive: float = 1.0, dx: float = 1.0, m
                                    k, C.byref(s), _stream(stream))
     _check(st, "pm_solve_direction", soft=(PM_OK, PM_ERR_NOT_PERCOLATING, PM_ERR_NOT_CONVERGED))
     return {"k_col": np.array(k[:]), "u": u, "p": p, "stats": s.as_dict(), "status": st}
+
+
+def principal_axes(k):
+    """Principal permeabilities (ascending) and axes (columns) of the symmetric part of a
+    3x3 tensor (pm_principal_axes; host only)."""
+    kk = (C.c_double * 9)(*[float(v) for v in np.asarray(k, dtype=np.float64).reshape(9)])
+    lam = (C.c_double * 3)()
+    ax = (C.c_double * 9)()
+    _check(load().pm_principal_axes(kk, lam, ax), "pm_principal_axes")
+    return np.array(lam[:]), np.array(ax[:]).reshape(3, 3)
+
+
+ISOTROPY, TRANSVERSE_ANISOTROPY, ORTHOTROPY = 0, 1, 2
+
+
+def anisotropy_class(lam, rel_tol: float = 1e-2) -> int:
+    """Sec. 2 material class of three principal permeabilities (pm_anisotropy_class)."""
+    v = (C.c_double * 3)(*[float(x) for x in lam])
+    c = int(load().pm_anisotropy_class(v, float(rel_tol)))
+    if c < 0:
+        raise ValueError("invalid principal permeabilities or tolerance")
+    return c
 
 
 def permeability_tensor(mask, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts):

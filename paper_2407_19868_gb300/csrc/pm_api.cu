@@ -1302,6 +1302,77 @@ const char *pm_strerror(int s) {
 
 int pm_version(void) { return kVersion; }
 
+// Sec. 2: eigenvalues / eigenvectors of the symmetric part of k by cyclic Jacobi
+// rotations (each rotation zeroes one off-diagonal pair; sweeps until the off-diagonal
+// mass is below machine precision relative to the diagonal).
+int pm_principal_axes(const double k[9], double lambda[3], double axes[9]) {
+    if (!k || !lambda) return PM_ERR_INVALID_ARG;
+    double a[3][3], v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (!std::isfinite(k[3 * i + j])) return PM_ERR_INVALID_ARG;
+            a[i][j] = 0.5 * (k[3 * i + j] + k[3 * j + i]);
+        }
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            diag += a[i][i] * a[i][i];
+            for (int j = i + 1; j < 3; ++j) off += a[i][j] * a[i][j];
+        }
+        if (off <= 1e-34 * diag || off == 0.0) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (a[p][q] == 0.0) continue;
+                // rotation angle that zeroes a[p][q]: tan(2 theta) = 2 a_pq / (a_qq - a_pp)
+                const double theta = 0.5 * (a[q][q] - a[p][p]) / a[p][q];
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < 3; ++r) {  // columns p, q of a
+                    const double arp = a[r][p], arq = a[r][q];
+                    a[r][p] = c * arp - s * arq;
+                    a[r][q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < 3; ++r) {  // rows p, q
+                    const double apr = a[p][r], aqr = a[q][r];
+                    a[p][r] = c * apr - s * aqr;
+                    a[q][r] = s * apr + c * aqr;
+                }
+                for (int r = 0; r < 3; ++r) {
+                    const double vrp = v[r][p], vrq = v[r][q];
+                    v[r][p] = c * vrp - s * vrq;
+                    v[r][q] = s * vrp + c * vrq;
+                }
+            }
+    }
+    int ord[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (a[ord[j]][ord[j]] < a[ord[i]][ord[i]]) std::swap(ord[i], ord[j]);
+    for (int j = 0; j < 3; ++j) {
+        const int c = ord[j];
+        lambda[j] = a[c][c];
+        if (!axes) continue;
+        int big = 0;
+        for (int i = 1; i < 3; ++i)
+            if (std::fabs(v[i][c]) > std::fabs(v[big][c])) big = i;
+        const double sg = v[big][c] < 0 ? -1.0 : 1.0;
+        for (int i = 0; i < 3; ++i) axes[3 * i + j] = sg * v[i][c];
+    }
+    return PM_OK;
+}
+
+int pm_anisotropy_class(const double lambda[3], double rel_tol) {
+    if (!lambda || !(rel_tol >= 0)) return -1;
+    double m = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        if (!std::isfinite(lambda[i])) return -1;
+        m = std::fmax(m, std::fabs(lambda[i]));
+    }
+    auto eq = [&](double x, double y) { return std::fabs(x - y) <= rel_tol * m; };
+    const int n = eq(lambda[0], lambda[1]) + eq(lambda[0], lambda[2]) + eq(lambda[1], lambda[2]);
+    return n >= 2 ? 0 : (n == 1 ? 1 : 2);
+}
+
 double pm_time_step(const pm_options *o) { return o ? time_step(o) : 0.0; }
 
 int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_options *o, int64_t n, void *u, void *p,

@@ -210,6 +210,19 @@ def sc_sphere(L: int, a: float) -> np.ndarray:
     return m
 
 
+def rotated_ellipsoid(n: int = 100, semi=(35.0, 10.0, 35.0), alpha_deg: float = 0.0) -> np.ndarray:
+    """Anisotropy benchmark of Sec. 6: one solid ellipsoid with semi-axes (a, b, c) along
+    (e1, e2, e3) centred in an n^3 periodic box and rotated about e1 by alpha (right-handed:
+    its e3 axis turns towards -e2); a voxel is solid when its centre lies inside."""
+    x = np.arange(n) + 0.5 - n / 2.0
+    z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+    t = np.radians(alpha_deg)
+    yb = np.cos(t) * y + np.sin(t) * z   # body coordinates (rotation by -alpha)
+    zb = -np.sin(t) * y + np.cos(t) * z
+    a, b, c = semi
+    return ((xx / a) ** 2 + (yb / b) ** 2 + (zb / c) ** 2 <= 1.0).astype(np.uint8)
+
+
 def random_blocks(shape, solid_fraction: float, seed: int) -> np.ndarray:
     """Independent random voxels, solid with probability ``solid_fraction``."""
     g = rng(seed)
