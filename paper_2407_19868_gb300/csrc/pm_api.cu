@@ -553,7 +553,9 @@ struct Monitor {
     double q_prev[3] = {0, 0, 0};
     double d_prev = -1.0, d_best = INFINITY;
     double delta = INFINITY, err = INFINITY;
-    int stalled = 0;  // consecutive windows without a new smallest change
+    int stalled = 0;  // consecutive windows without a new smallest change (any decrease counts:
+                      // a slow but steady convergence keeps setting new minima, while at
+                      // the FP32 floor the change only fluctuates)
     bool converged = false;
     // Window criterion (reading of Sec. 7.1, eps = delta|q| / |q|): relative change of
     // the mean velocity over one window, and its geometric-tail extrapolation.  ref > 0
@@ -572,7 +574,7 @@ struct Monitor {
         } else
             err = INFINITY;
         d_prev = delta;
-        if (delta < 0.9 * d_best) {
+        if (delta < d_best) {
             d_best = delta;
             stalled = 0;
         } else

@@ -258,3 +258,14 @@ def test_schedule_reported_and_converged_k_unchanged(api):
     assert a["stats"]["schedule"] == -1 and b["stats"]["schedule"] == 7
     assert a["stats"]["iters"] == b["stats"]["iters"]
     np.testing.assert_allclose(a["k_col"], b["k_col"], rtol=1e-12, atol=1e-14)
+
+
+def test_defect_correction_on_a_slowly_converging_geometry(api):
+    """A dilute obstacle converges slowly (each window shrinks the change by only a few
+    per cent); the defect correction must not mistake that for the FP32 floor."""
+    m = G.sc_sphere(32, 4.0)
+    d = torch.from_numpy(m).cuda()
+    r64 = api.solve_direction(d, 0, fields=False, precision="fp64", tol=1e-10, check_every=100)
+    rdc = api.solve_direction(d, 0, fields=False, precision="dc64", tol=1e-9, check_every=100)
+    assert r64["status"] == api.PM_OK and rdc["status"] == api.PM_OK
+    assert rdc["k_col"][0] == pytest.approx(r64["k_col"][0], rel=1e-7)
