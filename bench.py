@@ -363,6 +363,30 @@ def run_ellipsoid(args):
     return 0
 
 
+def run_thin(args):
+    """Regular thin porous media of Sec. 6 (Table sfb_domain_comparison): one cylinder per
+    1 mm x 1 mm periodic cell, dx = 4 um (250 x 250 voxels), radii 0.35 .. 0.49 mm; k_11
+    for a uniform (2-D) cell 4 voxels thick, and for the 27-voxel-thick cell with a 2-voxel
+    solid frame at both ends of e2; FP32 fields, the paper's criterion 1e-6."""
+    import torch
+    from paper_2407_19868_gb300 import api, geometry as G
+    api.load()
+    dx = 4e-6
+    paper = {0.35: 26.1, 0.40: 17.5, 0.45: 8.08, 0.47: 3.83, 0.49: 0.39}  # 1e-10 m^2
+    for rad_mm, kp in paper.items():
+        row = {"radius_mm": rad_mm, "paper_k11_1e-10m2": kp}
+        for name, ny, frame in (("2d", 4, 0), ("frame27", 27, 2)):
+            m = G.cylinder_cell(250, rad_mm * 1e-3 / dx, ny, frame)
+            t = time.perf_counter()
+            r = api.solve_direction(torch.from_numpy(m).cuda(), 0, dx=dx, fields=False, tol=1e-6,
+                                    precision="fp32")
+            torch.cuda.synchronize()
+            row[name] = {"k11_1e-10m2": float(r["k_col"][0]) * 1e10, "porosity": float(1 - m.mean()),
+                         "iters": r["stats"]["iters"], "status": r["status"], "seconds": time.perf_counter() - t}
+        print(json.dumps(row), flush=True)
+    return 0
+
+
 def run_sequence(args):
     """Precipitation-sequence measurement: a 1536 x 768 disk image (radii 12..30, porosity
     0.55), 24 states of random solid growth to porosity 0.30, extruded to 4 fluid layers
@@ -448,6 +472,7 @@ def main():
     ap.add_argument("--large-max-iter", type=int, default=40000)
     ap.add_argument("--sequence", action="store_true", help="batched precipitation-sequence measurement, then exit")
     ap.add_argument("--ellipsoid", action="store_true", help="rotated-ellipsoid anisotropy benchmark, then exit")
+    ap.add_argument("--thin", action="store_true", help="thin porous media (cylinder cells) benchmark, then exit")
     ap.add_argument("--seq-max-iter", type=int, default=4001)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling case: this many iterations of the benchmark solve, then exit")
@@ -460,6 +485,8 @@ def main():
         return run_sequence(args)
     if args.ellipsoid:
         return run_ellipsoid(args)
+    if args.thin:
+        return run_thin(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -223,6 +223,20 @@ def rotated_ellipsoid(n: int = 100, semi=(35.0, 10.0, 35.0), alpha_deg: float = 
     return ((xx / a) ** 2 + (yb / b) ** 2 + (zb / c) ** 2 <= 1.0).astype(np.uint8)
 
 
+def cylinder_cell(n: int, radius: float, ny: int, frame: int = 0) -> np.ndarray:
+    """Regular thin porous medium of Sec. 6 ("2D microfluidic" unit cell): one solid
+    cylinder of ``radius`` voxels with its axis along e2, centred in an n x n (e1, e3) cell,
+    ``ny`` voxels thick along e2, the outer ``frame`` layers at both e2 ends solid.  Shape
+    [n][ny][n] (z = e3, y = e2, x = e1)."""
+    x = np.arange(n) + 0.5 - n / 2.0
+    disk = (x[:, None] ** 2 + x[None, :] ** 2 <= radius * radius)  # [z][x]
+    m = np.broadcast_to(disk[:, None, :], (n, ny, n)).astype(np.uint8).copy()
+    if frame > 0:
+        m[:, :frame, :] = 1
+        m[:, ny - frame:, :] = 1
+    return m
+
+
 def random_blocks(shape, solid_fraction: float, seed: int) -> np.ndarray:
     """Independent random voxels, solid with probability ``solid_fraction``."""
     g = rng(seed)
