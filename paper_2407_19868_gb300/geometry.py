@@ -237,6 +237,34 @@ def cylinder_cell(n: int, radius: float, ny: int, frame: int = 0) -> np.ndarray:
     return m
 
 
+_LATTICE = {
+    "sc": [(0.0, 0.0, 0.0)],
+    "bcc": [(0.0, 0.0, 0.0), (0.5, 0.5, 0.5)],
+    "fcc": [(0.0, 0.0, 0.0), (0.5, 0.5, 0.0), (0.5, 0.0, 0.5), (0.0, 0.5, 0.5)],
+}
+
+
+def regular_pack(L: int, kind: str, target_porosity: float):
+    """Regular sphere packing of Sec. 6 in a periodic cubic unit cell of L voxels: spheres of
+    one radius on the simple-cubic, body-centred or face-centred lattice sites (overlapping
+    below the touching porosity).  The radius is the quantile of the distance of voxel
+    centres to the nearest site at which the voxel porosity (centres inside a sphere are
+    solid) reaches the target; voxels at equal distance go together, so small cells land
+    within a per cent or two of it.  Returns (mask, radius in voxels)."""
+    x = np.arange(L) + 0.5
+    z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+    d2 = np.full((L, L, L), np.inf)
+    for (sx, sy, sz) in _LATTICE[kind]:
+        dx = np.abs(xx - sx * L); dx = np.minimum(dx, L - dx)
+        dy = np.abs(y - sy * L); dy = np.minimum(dy, L - dy)
+        dz = np.abs(z - sz * L); dz = np.minimum(dz, L - dz)
+        d2 = np.minimum(d2, dx * dx + dy * dy + dz * dz)
+    d = np.sqrt(d2).ravel()
+    n_solid = int(round((1.0 - target_porosity) * d.size))
+    r = float(np.sort(d)[n_solid - 1]) if n_solid > 0 else 0.0
+    return (np.sqrt(d2) <= r).astype(np.uint8), r
+
+
 def random_blocks(shape, solid_fraction: float, seed: int) -> np.ndarray:
     """Independent random voxels, solid with probability ``solid_fraction``."""
     g = rng(seed)

@@ -1,4 +1,5 @@
-"""The anisotropy benchmark geometry of Sec. 6 (an inclined ellipsoid in a periodic box).
+"""Benchmark geometries of Sec. 6: the inclined ellipsoid in a periodic box and regular
+sphere packings.
 
 CPU: the generator's volume is the ellipsoid's, and a 90 degree rotation about e1 equals
 swapping e2 and e3 exactly.  GPU: the full k tensor of a coarse inclined ellipsoid (large
@@ -37,3 +38,29 @@ def test_inclined_ellipsoid_ktensor_matches_oracle(oracle_mod):
     j = int(np.argmax(lam))
     phi = np.degrees(np.arctan2(abs(R[1, j]), abs(R[2, j])))
     assert 15.0 < phi < 40.0  # follows the 30 degree inclination (22 degrees at b = 2.4 voxels)
+
+
+@pytest.mark.parametrize("kind", ["sc", "bcc", "fcc"])
+def test_regular_pack_porosity_and_cubic_symmetry(kind):
+    m, r = G.regular_pack(24, kind, 0.5)
+    assert abs(G.porosity(m) - 0.5) < 0.02 and r > 0  # ties of equal distance at L = 24
+    assert np.array_equal(m, np.transpose(m, (1, 2, 0))) and np.array_equal(m, m[::-1, ::-1, ::-1])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["sc", "bcc", "fcc"])
+def test_regular_pack_ktensor_is_isotropic(kind):
+    """The cubic lattices give k = k_11 I exactly on the discrete grid (axis permutations
+    map the geometry onto itself); the GPU tensor shows it to the FP32 floor."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():  # pragma: no cover
+        pytest.skip("no CUDA device")
+    from paper_2407_19868_gb300 import api
+    m, _ = G.regular_pack(32, kind, 0.5)
+    r = api.permeability_tensor(torch.from_numpy(m).cuda(), precision="fp32", tol=1e-8)
+    k = np.asarray(r["k_raw"])
+    kd = np.mean(np.diag(k))
+    assert np.max(np.abs(np.diag(k) - kd)) < 1e-5 * kd
+    assert np.max(np.abs(k - np.diag(np.diag(k)))) < 1e-5 * kd
+    lam, _ = api.principal_axes(k)
+    assert api.anisotropy_class(lam, rel_tol=1e-4) == api.ISOTROPY
