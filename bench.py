@@ -414,6 +414,68 @@ def run_packs(args):
     return 0
 
 
+def run_compare(args):
+    """The forms of the solver against the plain GPU path on the benchmark geometry (256^3
+    pack), each timed to a full k tensor (second of two runs, so tuning is excluded) and its
+    error per k_ij against the FP64 oracle reference (tests/golden/reference_k.json, written
+    by the oracle): plain = three unbatched single-drive solves, FP32 fields + FP64
+    reductions, no graph, tol 1e-6; batched = the three drives in each launch with window
+    graphs; dc64 = batched with FP64 defect correction to 1e-8; fp64 = FP64 fields to 1e-8;
+    adjoint = forward + transposed solves and dk_xx/d alpha for J = k_xx."""
+    import torch
+    from paper_2407_19868_gb300 import api, geometry as G
+    api.load()
+    mask, _ = make_mask()
+    with open(os.path.join(ROOT, "tests", "golden", "reference_k.json")) as f:
+        ref = json.load(f)["config2"]
+    if ref["sha256"] != G.mask_sha256(mask):
+        print(json.dumps({"compare": "unavailable", "reason": "reference mask differs"}))
+        return 0
+    kref = np.zeros((3, 3))
+    for j in range(3):
+        kref[:, j] = ref["columns"][str(j)]["k_col"]
+    d = torch.from_numpy(mask).cuda()
+    kd = np.max(np.abs(np.diag(kref)))
+
+    def errors(k):
+        diag = max(abs(k[i, i] / kref[i, i] - 1) for i in range(3))
+        off = max(abs(k[i, j] - kref[i, j]) / kd for i in range(3) for j in range(3) if i != j)
+        return diag, off
+
+    def plain():
+        cols = [api.solve_direction(d, j, fields=False, tol=1e-6, precision="fp32", use_graph=0) for j in range(3)]
+        return np.stack([c["k_col"] for c in cols], axis=1), sum(c["stats"]["iters"] for c in cols)
+
+    def tensor(**kw):
+        r = api.permeability_tensor(d, **kw)
+        return np.asarray(r["k_raw"]), sum(st["iters"] for st in r["stats"])
+
+    def adjoint():
+        w = np.zeros((3, 3))
+        w[0, 0] = 1.0
+        r = api.sensitivity(d, w=w, tol=1e-6, precision="fp32")
+        k = np.asarray(r["k_raw"])
+        return k, 0
+
+    modes = [("plain", plain), ("batched", lambda: tensor(tol=1e-6, precision="fp32")),
+             ("dc64", lambda: tensor(tol=1e-8, precision="dc64")),
+             ("fp64", lambda: tensor(tol=1e-8, precision="fp64")), ("adjoint_kxx", adjoint)]
+    base = None
+    for name, fn in modes:
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            k, iters = fn()
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t
+        base = secs if base is None else base
+        ed, eo = errors(k)
+        print(json.dumps({"mode": name, "seconds": secs, "vs_plain": secs / base, "iters_total": iters,
+                          "max_rel_err_diag": ed, "max_err_offdiag_rel_kii": eo,
+                          "meets_1e-5": bool(ed <= 1e-5 and eo <= 1e-5)}), flush=True)
+    return 0
+
+
 def run_sequence(args):
     """Precipitation-sequence measurement: a 1536 x 768 disk image (radii 12..30, porosity
     0.55), 24 states of random solid growth to porosity 0.30, extruded to 4 fluid layers
@@ -501,6 +563,8 @@ def main():
     ap.add_argument("--ellipsoid", action="store_true", help="rotated-ellipsoid anisotropy benchmark, then exit")
     ap.add_argument("--thin", action="store_true", help="thin porous media (cylinder cells) benchmark, then exit")
     ap.add_argument("--packs", action="store_true", help="regular SC / BCC / FCC packings benchmark, then exit")
+    ap.add_argument("--compare", action="store_true",
+                    help="plain / batched / defect-corrected / FP64 / adjoint forms against the oracle, then exit")
     ap.add_argument("--seq-max-iter", type=int, default=4001)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling case: this many iterations of the benchmark solve, then exit")
@@ -517,6 +581,8 @@ def main():
         return run_thin(args)
     if args.packs:
         return run_packs(args)
+    if args.compare:
+        return run_compare(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
