@@ -107,9 +107,11 @@ double now_s() {
     return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
+// Grid of a 256-thread grid-stride kernel over n items: enough blocks for every item, at
+// most 32 per SM.
 int launch_grid(long long n) {
-    long long b = (n + 255) / 256;
-    return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
+    const long long b = (n + 255) / 256, cap = 32ll * tiled_grid_size();
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 // ------------------------------------------------------------------ geometry
@@ -756,7 +758,7 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
     float *r32[kMaxBatch] = {nullptr, nullptr, nullptr, nullptr};
     double q64[kMaxBatch][3];
     int rc;
-    const int nb = 152 * 4;
+    const int nb = tiled_grid_size() * 4;
     double *part = nullptr;
     if ((rc = S.scr.alloc(&part, (size_t)S.nprob * nb * 4))) return rc;
     for (int k = 0; k < S.nprob; ++k) {
