@@ -245,6 +245,28 @@ PM_API int pm_batch_ktensor(int n_domains, const pm_domain *doms, const int32_t 
 PM_API int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *opt,
                           float *dJ_dalpha, double *J, double k_raw[9], void *cuda_stream);
 
+/* Pre-processing (Sec. 5 "Processing input data": mirroring for symmetric periodicity).
+ * Writes the mask followed by its mirror image along every axis whose bit is set in axes
+ * (bit 0 = x, 1 = y, 2 = z), so that the doubled domain is periodic and symmetric under
+ * the reflection (its k has no coupling between a mirrored axis and the others).
+ *   mask: nx*ny*nz bytes [nz][ny][nx]; out: (nx << mx)(ny << my)(nz << mz) bytes, caller-
+ *   owned, same layout; both host memory (on_device = 0, a plain loop on the host) or both
+ *   device memory (on_device = 1, one kernel on cuda_stream, returns after it finished).
+ *   Errors: PM_ERR_INVALID_ARG (NULL, sizes < 1, axes outside 0..7), PM_ERR_CUDA. */
+PM_API int pm_mirror_mask(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, int32_t axes,
+                          int32_t on_device, uint8_t *out, void *cuda_stream);
+
+/* Pre-processing (Sec. 5: elimination of disconnected pore spaces; host only).  Copies the
+ * mask to out and turns solid every face-connected component of pore cells that carries
+ * no flow through the domain: one that wraps around no periodic axis and does not join
+ * the first and the last layer of a PM_BC_PRESSURE axis (wall axes connect nothing).  Such
+ * pores hold u = 0 at the fixed point, so k is unchanged; the iteration loses unknowns.
+ *   mask, out: host, nx*ny*nz bytes [nz][ny][nx] (may be the same buffer).
+ *   bc: per axis PM_BC_*.  removed (may be NULL): number of pore cells turned solid.
+ *   Errors: PM_ERR_INVALID_ARG. */
+PM_API int pm_remove_isolated_pores(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, const int32_t bc[3],
+                                    uint8_t *out, int64_t *removed);
+
 /* Spectral form of a permeability tensor (Sec. 2, Eq. 3dK_eigen): principal permeabilities
  * lambda (ascending) and principal axes, from the symmetric part of k (host only, no GPU).
  *   k: host, 9 doubles, row-major.  lambda: host, 3 doubles out.

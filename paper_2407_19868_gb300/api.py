@@ -115,6 +115,9 @@ def load():
         L.pm_batch_ktensor.argtypes = [C.c_int, C.POINTER(Domain), C.POINTER(C.c_int32), C.POINTER(Options), dp, dp,
                                        C.POINTER(Stats), vp]
         L.pm_principal_axes.argtypes = [dp, dp, dp]
+        L.pm_mirror_mask.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
+        L.pm_remove_isolated_pores.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), vp,
+                                               C.POINTER(C.c_int64)]
         L.pm_anisotropy_class.argtypes = [dp, C.c_double]
         _LIB = L
         return L
@@ -219,6 +222,39 @@ def solve_direction(mask, drive_dir: int, drive: float = 1.0, dx: float = 1.0, m
                                    k, C.byref(s), _stream(stream))
     _check(st, "pm_solve_direction", soft=(PM_OK, PM_ERR_NOT_PERCOLATING, PM_ERR_NOT_CONVERGED))
     return {"k_col": np.array(k[:]), "u": u, "p": p, "stats": s.as_dict(), "status": st}
+
+
+def mirror_mask(mask, axes=(True, False, False), stream=None):
+    """Mask followed by its mirror image along the chosen axes (x, y, z) -- pre-processing
+    for symmetric periodicity (pm_mirror_mask).  numpy in, numpy out (host loop); a CUDA
+    uint8 tensor in, a CUDA tensor out (one kernel)."""
+    bits = sum(1 << a for a in range(3) if axes[a])
+    if hasattr(mask, "is_cuda") and mask.is_cuda:
+        import torch
+        m = mask.contiguous()
+        nz, ny, nx = m.shape
+        out = torch.empty((nz << bool(axes[2]), ny << bool(axes[1]), nx << bool(axes[0])), dtype=torch.uint8,
+                          device=m.device)
+        st = load().pm_mirror_mask(m.data_ptr(), nx, ny, nz, bits, 1, out.data_ptr(), _stream(stream))
+    else:
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        nz, ny, nx = m.shape
+        out = np.empty((nz << bool(axes[2]), ny << bool(axes[1]), nx << bool(axes[0])), dtype=np.uint8)
+        st = load().pm_mirror_mask(m.ctypes.data, nx, ny, nz, bits, 0, out.ctypes.data, None)
+    _check(st, "pm_mirror_mask")
+    return out
+
+
+def remove_isolated_pores(mask, bc=(0, 0, 0)):
+    """Mask with every pore component that carries no flow through the domain turned solid
+    (pm_remove_isolated_pores; host).  Returns (mask, number of cells removed)."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    nz, ny, nx = m.shape
+    out = np.empty_like(m)
+    n = C.c_int64(0)
+    _check(load().pm_remove_isolated_pores(m.ctypes.data, nx, ny, nz, (C.c_int32 * 3)(*bc), out.ctypes.data,
+                                           C.byref(n)), "pm_remove_isolated_pores")
+    return out, int(n.value)
 
 
 def principal_axes(k):

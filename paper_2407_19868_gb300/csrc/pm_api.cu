@@ -1365,6 +1365,91 @@ int pm_principal_axes(const double k[9], double lambda[3], double axes[9]) {
     return PM_OK;
 }
 
+int pm_mirror_mask(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, int32_t axes, int32_t on_device,
+                   uint8_t *out, void *cuda_stream) {
+    if (!mask || !out || nx < 1 || ny < 1 || nz < 1 || axes < 0 || axes > 7) return PM_ERR_INVALID_ARG;
+    const int mx = axes & 1, my = (axes >> 1) & 1, mz = (axes >> 2) & 1;
+    const long long ox = (long long)nx << mx, oy = (long long)ny << my, oz = (long long)nz << mz;
+    if (on_device) {
+        cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+        mirror_kernel<<<launch_grid(ox * oy * oz), 256, 0, s>>>(mask, nx, ny, nz, mx, my, mz, out);
+        PM_CK(cudaGetLastError());
+        PM_CK(cudaStreamSynchronize(s));
+        return PM_OK;
+    }
+    for (long long z = 0; z < oz; ++z)
+        for (long long y = 0; y < oy; ++y)
+            for (long long x = 0; x < ox; ++x) {
+                const long long sx = x < nx ? x : 2 * nx - 1 - x, sy = y < ny ? y : 2 * ny - 1 - y,
+                                sz = z < nz ? z : 2 * nz - 1 - z;
+                out[x + ox * (y + oy * z)] = mask[sx + nx * (sy + ny * sz)];
+            }
+    return PM_OK;
+}
+
+// Components of face-connected pore cells by breadth-first search; a component is kept
+// when it wraps a periodic axis (two paths to one cell that cross that boundary a
+// different number of times) or holds cells in both end layers of a fixed-pressure axis.
+int pm_remove_isolated_pores(const uint8_t *mask, int32_t nx, int32_t ny, int32_t nz, const int32_t bc[3],
+                             uint8_t *out, int64_t *removed) {
+    if (!mask || !out || !bc || nx < 1 || ny < 1 || nz < 1) return PM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (bc[a] != PM_BC_PERIODIC && bc[a] != PM_BC_WALL && bc[a] != PM_BC_PRESSURE) return PM_ERR_INVALID_ARG;
+    const long long N = (long long)nx * ny * nz;
+    const int n[3] = {nx, ny, nz};
+    std::vector<uint8_t> m(mask, mask + N), seen((size_t)N, 0);
+    std::vector<int16_t> wind((size_t)N * 3);
+    std::vector<long long> comp;
+    long long gone = 0;
+    for (long long s0 = 0; s0 < N; ++s0) {
+        if (m[s0] || seen[s0]) continue;
+        comp.clear();
+        comp.push_back(s0);
+        seen[s0] = 1;
+        wind[s0 * 3] = wind[s0 * 3 + 1] = wind[s0 * 3 + 2] = 0;
+        bool flows = false, lo[3] = {false, false, false}, hi[3] = {false, false, false};
+        for (size_t h = 0; h < comp.size(); ++h) {
+            const long long c = comp[h];
+            const int co[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = lo[a] || co[a] == 0;
+                hi[a] = hi[a] || co[a] == n[a] - 1;
+                for (int dm = -1; dm <= 1; dm += 2) {
+                    int cc[3] = {co[0], co[1], co[2]};
+                    int w = 0;
+                    cc[a] += dm;
+                    if (cc[a] < 0 || cc[a] >= n[a]) {
+                        if (bc[a] != PM_BC_PERIODIC) continue;
+                        w = cc[a] < 0 ? -1 : 1;
+                        cc[a] = (cc[a] + n[a]) % n[a];
+                    }
+                    const long long b = cc[0] + (long long)nx * (cc[1] + (long long)ny * cc[2]);
+                    if (m[b]) continue;
+                    int16_t wn[3] = {wind[c * 3], wind[c * 3 + 1], wind[c * 3 + 2]};
+                    wn[a] = (int16_t)(wn[a] + w);
+                    if (!seen[b]) {
+                        seen[b] = 1;
+                        for (int k = 0; k < 3; ++k) wind[b * 3 + k] = wn[k];
+                        comp.push_back(b);
+                    } else {
+                        for (int k = 0; k < 3; ++k)
+                            if (wind[b * 3 + k] != wn[k]) flows = true;
+                    }
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a)
+            if (bc[a] == PM_BC_PRESSURE && lo[a] && hi[a] && n[a] >= 2) flows = true;
+        if (!flows) {
+            for (long long c : comp) m[c] = 1;
+            gone += (long long)comp.size();
+        }
+    }
+    std::memcpy(out, m.data(), (size_t)N);
+    if (removed) *removed = gone;
+    return PM_OK;
+}
+
 int pm_anisotropy_class(const double lambda[3], double rel_tol) {
     if (!lambda || !(rel_tol >= 0)) return -1;
     double m = 0.0;

@@ -36,6 +36,25 @@ __global__ void classify_kernel(const uint8_t *__restrict__ mask, int nx, int ny
     }
 }
 
+// Pre-processing (Sec. 5, mirroring for symmetric periodicity): out, 2n long along every
+// axis with m_a = 1, holds the mask followed by its reflection, so the doubled domain is
+// periodic.
+__global__ void mirror_kernel(const uint8_t *__restrict__ in, int nx, int ny, int nz, int mx, int my, int mz,
+                              uint8_t *__restrict__ out) {
+    const int ox = nx << mx, oy = ny << my, oz = nz << mz;
+    const long long M = (long long)ox * oy * oz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < M;
+         c += (long long)gridDim.x * blockDim.x) {
+        int x = (int)(c % ox);
+        const long long r = c / ox;
+        int y = (int)(r % oy), z = (int)(r / oy);
+        if (x >= nx) x = 2 * nx - 1 - x;
+        if (y >= ny) y = 2 * ny - 1 - y;
+        if (z >= nz) z = 2 * nz - 1 - z;
+        out[c] = in[(long long)x + (long long)nx * ((long long)y + (long long)ny * z)];
+    }
+}
+
 // Zero the values on non-fluid faces and solid cells (the invariant every sweep relies
 // on), used on caller-provided starting fields.
 template <typename T>
