@@ -200,3 +200,26 @@ def test_hasimoto_dilute_sc_array(oracle_mod):
         errs.append(abs(r["q"][0] / oracle_mod.RE_PAPER / k_h - 1.0))
     assert errs[1] < errs[0]
     assert errs[1] < 0.10
+
+
+def _white_rect_duct_flux(a, b, terms=200):
+    """Series for the flux of a rectangular duct of height 2a, width 2b (b >= a) with
+    nabla^2 w = -1 and w = 0 on the walls (White, Viscous Fluid Flow)."""
+    s = sum(np.tanh(i * np.pi * b / (2 * a)) / i ** 5 for i in range(1, 2 * terms, 2))
+    return 4.0 * b * a ** 3 / 3.0 * (1.0 - 192.0 * a / (np.pi ** 5 * b) * s)
+
+
+def test_rectangular_duct_converges_to_series(oracle_mod):
+    """Sec. 6.1 rectangular channel (width b = 2h): the discrete flux approaches the series
+    solution with second order as h/dx grows (one solid layer closes the periodic cell)."""
+    errs = []
+    for h in (5, 10, 20):
+        m = np.ones((2 * h + 1, h + 1, 2), dtype=np.uint8)
+        m[:2 * h, :h, :] = 0  # h fluid voxels along y, 2h along z, uniform along x
+        dom = oracle_mod.Domain(m)
+        r = dom.solve(0, tol=1e-12, check_every=100)
+        Q = r["q"][0] * m.size / m.shape[2] / oracle_mod.RE_PAPER  # flux of one x-plane
+        errs.append(Q / _white_rect_duct_flux(h / 2.0, float(h)) - 1.0)
+    assert 0 < errs[2] < errs[1] < errs[0]
+    assert errs[1] / errs[2] > 3.5          # second order
+    assert errs[1] < 5e-3                    # 10 x 20 voxels: within half a per cent
