@@ -223,3 +223,42 @@ def test_rectangular_duct_converges_to_series(oracle_mod):
     assert 0 < errs[2] < errs[1] < errs[0]
     assert errs[1] / errs[2] > 3.5          # second order
     assert errs[1] < 5e-3                    # 10 x 20 voxels: within half a per cent
+
+
+def _one_step_map_spectral_radius(oracle_mod, mask, dt):
+    """Spectral radius of the homogeneous one-step map of Algorithm 1 (velocity update,
+    then pressure from the new velocity), assembled by probing the oracle with unit vectors
+    of the fluid unknowns."""
+    dom = oracle_mod.Domain(mask)
+    nf, _ = dom.tables()
+    iu = [np.flatnonzero(nf[d].ravel()) for d in range(3)]
+    ip = np.flatnonzero((mask == 0).ravel())
+    cols = [(0, d, k) for d in range(3) for k in iu[d]] + [(1, 0, k) for k in ip]
+    M = np.zeros((len(cols), len(cols)))
+    for j, (kind, d, k) in enumerate(cols):
+        U, p = dom.zeros()
+        if kind == 0:
+            U[d].reshape(-1)[k] = 1.0
+        else:
+            p.reshape(-1)[k] = 1.0
+        dom.iterate(U, p, 1, drive_dir=0, drive=0.0, dt=dt)
+        M[:, j] = np.concatenate([U[d].reshape(-1)[iu[d]] for d in range(3)] + [p.reshape(-1)[ip]])
+    return np.max(np.abs(np.linalg.eigvals(M)))
+
+
+@pytest.mark.parametrize("name,make", [
+    ("open", lambda: np.zeros((4, 4, 4), dtype=np.uint8)),
+    ("ducts", lambda: G.square_duct(4, 1, 2)),
+    ("blocks", lambda: G.random_blocks((5, 5, 6), 0.3, seed=1)),
+    ("spheres", lambda: G.overlapping_spheres((6, 6, 6), 1.5, 0.6, seed=3)),
+])
+def test_time_step_reading_is_stable_and_near_sharp(oracle_mod, name, make):
+    """The pseudo-time step is not stated in the paper; the reading (the root of
+    12 c^2 dt^2 + 40 dt / Re - 4 = 0, times 0.9) must make the iteration map
+    non-expansive on any geometry (eigenvalue 1 only for the constant-pressure gauge
+    modes) and should not be far below the true limit: 1.5 times the root diverges."""
+    mask = make()
+    root = oracle_mod.default_dt(safety=1.0)
+    for f in (0.9, 1.0):
+        assert _one_step_map_spectral_radius(oracle_mod, mask, f * root) <= 1.0 + 1e-9
+    assert _one_step_map_spectral_radius(oracle_mod, mask, 1.5 * root) > 1.05
