@@ -64,3 +64,20 @@ def test_regular_pack_ktensor_is_isotropic(kind):
     assert np.max(np.abs(k - np.diag(np.diag(k)))) < 1e-5 * kd
     lam, _ = api.principal_axes(k)
     assert api.anisotropy_class(lam, rel_tol=1e-4) == api.ISOTROPY
+
+
+@pytest.mark.gpu
+@pytest.mark.slow
+def test_ellipsoid_anisotropy_ratio_of_the_paper():
+    """Sec. 6, Table ellipse_allvalues at alpha = 0: k_33 / k_22 = 9.43 / 3.85 = 2.45 and
+    k_III / k_II = 9.46 / 3.81 = 2.48 for the 100^3 box with the (35, 10, 35) ellipsoid; the
+    paper's absolute values are not comparable (units), its ratio is."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():  # pragma: no cover
+        pytest.skip("no CUDA device")
+    from paper_2407_19868_gb300 import api
+    m = G.rotated_ellipsoid(100, (35.0, 10.0, 35.0), 0.0)
+    r = api.permeability_tensor(torch.from_numpy(m).cuda(), precision="fp32", tol=1e-6)
+    assert r["status"] == api.PM_OK
+    k = np.asarray(r["k"])
+    assert 2.43 < k[2, 2] / k[1, 1] < 2.53
