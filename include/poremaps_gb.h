@@ -30,8 +30,11 @@
  *     its work; device outputs are complete on cuda_stream when the call returns.
  *   - Ownership: the caller owns every pointer it passes and keeps device pointers valid
  *     for the call; the library never frees caller memory.  Scratch (ping-pong fields,
- *     neighbourhood flags, FP64 master copies, reduction buffers) is allocated with
- *     cudaMallocAsync inside each call and released before it returns.
+ *     neighbourhood codes, FP64 master copies, reduction buffers) comes from the
+ *     library's own stream-ordered memory pool (one per device) inside each call and
+ *     goes back to that pool before the call returns; the pool keeps it reserved for the
+ *     next call (no allocation cost when the same or a smaller domain comes again) until
+ *     pm_release_memory hands it back to the driver.
  *   - Errors: every function returns a pm_status; nothing throws or aborts.  On an error
  *     return, outputs may be partially written.
  */
@@ -108,7 +111,9 @@ typedef struct pm_options {
     double Re;                /* Reynolds number (Sec. 4: 0.01) */
     double c2;                /* squared artificial speed of sound (Sec. 4: 1.5e6) */
     int32_t use_graph;        /* 1: replay each window as a captured CUDA graph */
-    int32_t check_percolation;/* 1: host breadth-first search before solving */
+    int32_t check_percolation;/* 1: percolation search before solving (device union-find
+                                 of the pore cells, winding search on the host over the
+                                 components that meet at the periodic faces) */
     double dc_switch_tol;     /* PM_FP32_DC64: leave plain FP32 sweeps at this change */
     int32_t dc_max_rounds;    /* PM_FP32_DC64: maximum correction rounds */
     int32_t kernel;           /* 0 = default sweep kernel, 1 = simple reference kernel */
@@ -136,13 +141,25 @@ typedef struct pm_stats {
     int32_t percolates;       /* 1 if a fluid path wraps the domain along the drive */
     int32_t schedule;         /* tiled kernel's work split used (-1 persistent, n > 0 chunks
                                  of n planes; 0 = simple kernel or multi-geometry batch) */
-    int32_t reserved[4];
+    double setup_seconds;     /* wall time from the call's entry to its first sweep (mask
+                                 ingest, neighbourhood, percolation, allocation) */
+    int64_t n_fluid;          /* pore voxels of the domain */
+    double sweep_ms_src;      /* as sweep_ms for the sweeps that carry a source term (the
+                                 correction solves of PM_FP32_DC64); sweep_ms then covers
+                                 the plain FP32 phase only */
+    int64_t sweeps_timed_src; /* sweeps inside those timed windows */
+    int64_t kernel_launches;  /* kernels launched by the call (a replayed window graph counts
+                                 the kernels it holds) */
 } pm_stats;
 
 /* Fills *opt with the defaults: tol 1e-6, check_every 200, max_iter 2e6,
  * PM_FP32_RED64, dt_safety 0.9, Re 0.01, c2 1.5e6, graphs on, percolation check on,
  * dc_switch_tol 1e-5, dc_max_rounds 8, autotune on. */
 PM_API void pm_default_options(pm_options *opt);
+
+/* Returns the scratch memory that the library's pool keeps between calls on the current
+ * device to the driver (memory of calls still running stays).  Errors: PM_ERR_CUDA. */
+PM_API int pm_release_memory(void);
 
 /* Human-readable text of a pm_status (static storage). */
 PM_API const char *pm_strerror(int status);
@@ -170,8 +187,13 @@ PM_API int pm_iterate(const pm_domain *dom, int dir, double drive, const pm_opti
  * under another allocator that has already reserved the GPU's memory (a framework's
  * caching allocator), or a latency-critical loop in which cudaMalloc / cudaFree would
  * synchronise the device.
- *   Same arguments, units, results and errors as pm_iterate; u and p are updated in place.
- *   Limit: nx * ny * nz <= 131072 cells (e.g. 64 x 64 x 32), else PM_ERR_TOO_LARGE.
+ *   Same arguments, units and results as pm_iterate (the same kernels with the same work
+ *   split: opt->kernel and opt->schedule are honoured, opt->autotune is ignored -- a
+ *   schedule of 0 means persistent CTAs); u and p are updated in place.
+ *   u and p must start on 16-byte boundaries (they are one buffer of the ping-pong pair).
+ *   Errors as pm_iterate, and: PM_ERR_TOO_LARGE above nx * ny * nz = 131072 cells (e.g.
+ *   64 x 64 x 32); PM_ERR_UNSUPPORTED for a PM_BC_PRESSURE axis (pm_iterate takes it);
+ *   PM_ERR_INVALID_ARG for u or p off a 16-byte boundary.
  *   Scratch: a fixed 5 MB device array inside the library (a copy of the mask, the
  *   neighbourhood codes and the second field buffer).  Every GPU that loads the library
  *   holds it until the process exits.  The first call on a device looks up its device

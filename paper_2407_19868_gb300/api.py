@@ -39,7 +39,8 @@ _PRECISION = {"fp32": FP32_RED64, "fp32_red64": FP32_RED64, "fp32_dc64": FP32_DC
 # every function the header declares (checked by the ABI test)
 EXPORTED = ["pm_default_options", "pm_strerror", "pm_version", "pm_time_step", "pm_iterate",
             "pm_iterate_noalloc", "pm_solve_direction", "pm_permeability_tensor", "pm_sensitivity",
-            "pm_batch_ktensor"]
+            "pm_batch_ktensor", "pm_mirror_mask", "pm_remove_isolated_pores", "pm_principal_axes",
+            "pm_anisotropy_class", "pm_release_memory"]
 
 
 class PMError(RuntimeError):
@@ -67,7 +68,8 @@ class Stats(C.Structure):
                 ("err_est", C.c_double), ("div_res", C.c_double), ("seconds", C.c_double),
                 ("sweep_ms", C.c_double), ("sweeps_timed", C.c_int64), ("dc_rounds", C.c_int32),
                 ("status", C.c_int32), ("percolates", C.c_int32), ("schedule", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("setup_seconds", C.c_double), ("n_fluid", C.c_int64), ("sweep_ms_src", C.c_double),
+                ("sweeps_timed_src", C.c_int64), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {"iters": int(self.iters), "q": [float(v) for v in self.q], "delta": float(self.delta),
@@ -75,7 +77,9 @@ class Stats(C.Structure):
                 "seconds": float(self.seconds), "sweep_ms": float(self.sweep_ms),
                 "sweeps_timed": int(self.sweeps_timed), "dc_rounds": int(self.dc_rounds),
                 "status": int(self.status), "percolates": bool(self.percolates),
-                "schedule": int(self.schedule)}
+                "schedule": int(self.schedule), "setup_seconds": float(self.setup_seconds),
+                "n_fluid": int(self.n_fluid), "sweep_ms_src": float(self.sweep_ms_src),
+                "sweeps_timed_src": int(self.sweeps_timed_src), "kernel_launches": int(self.kernel_launches)}
 
 
 _LIB = None
@@ -119,8 +123,15 @@ def load():
         L.pm_remove_isolated_pores.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32), vp,
                                                C.POINTER(C.c_int64)]
         L.pm_anisotropy_class.argtypes = [dp, C.c_double]
+        L.pm_release_memory.restype = C.c_int
         _LIB = L
         return L
+
+
+def release_memory():
+    """Hand the scratch the library's memory pool keeps between calls back to the driver
+    (pm_release_memory, current device)."""
+    _check(load().pm_release_memory(), "pm_release_memory")
 
 
 def strerror(status: int) -> str:

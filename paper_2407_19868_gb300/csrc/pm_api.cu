@@ -2,7 +2,8 @@
 //
 // Call flow of a solve (Algorithm 1 of the paper, one GPU, no halo exchange):
 //   mask -> device -> neighbourhood flags (classify_kernel)
-//   -> percolation check (host breadth-first search, Sec. 5.1 assumes percolation)
+//   -> percolation check (device union-find over the pore cells plus a winding search on
+//      the small graph of components, Sec. 5.1 assumes percolation)
 //   -> first sweep (velocity of iteration 1)
 //   -> windows of M fused sweeps, the last one with FP64 block sums, captured once as a
 //      CUDA graph and replayed; after each window 4 doubles per drive come back to the
@@ -18,18 +19,20 @@
 #include <algorithm>
 #include <array>
 #include <mutex>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
 #include "../../include/poremaps_gb.h"
 #include "pm_kernels.cuh"
+#include "pm_percolation.cuh"
 #include "pm_sweep_tiled.cuh"
 
 using namespace pmgb;
 
 namespace {
 
-constexpr int kVersion = 100;  // 0.1.0
+constexpr int kVersion = 200;  // 0.2.0
 
 struct Status {
     int code = PM_OK;
@@ -50,7 +53,43 @@ int map_cuda(cudaError_t e) {
         }                                                \
     } while (0)
 
-// Stream-ordered scratch that is released when the owner goes out of scope.
+// Stream-ordered memory pool of the library, one per device, created on first use.  Its
+// release threshold is unlimited, so scratch freed at the end of a call stays reserved
+// for the next call of the same or a smaller size instead of going back to the driver
+// (pm_release_memory returns it).
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+int library_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    PM_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return PM_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        PM_CK(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~0ull;
+        cudaError_t e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaMemPoolDestroy(pool);
+            return map_cuda(e);
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return PM_OK;
+}
+
+// Stream-ordered scratch from the library pool, freed (back into the pool) when the
+// owner goes out of scope.
 struct Scratch {
     cudaStream_t s = nullptr;
     std::vector<void *> ptrs;
@@ -60,11 +99,14 @@ struct Scratch {
     }
     template <typename T>
     int alloc(T **p, size_t count) {
+        *p = nullptr;
+        cudaMemPool_t pool = nullptr;
+        int st = library_pool(&pool);
+        if (st) return st;
         void *v = nullptr;
-        cudaError_t e = cudaMallocAsync(&v, count * sizeof(T) + 16, s);
+        cudaError_t e = cudaMallocFromPoolAsync(&v, count * sizeof(T) + 16, pool, s);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
-            *p = nullptr;
             return map_cuda(e);
         }
         ptrs.push_back(v);
@@ -72,6 +114,34 @@ struct Scratch {
         return PM_OK;
     }
 };
+
+// Small pinned host blocks for the per-window reduction results, kept for reuse (a
+// cudaMallocHost per solve would cost more than the solve of a small domain).
+constexpr size_t kPinnedBlock = 4096;
+std::mutex g_pinned_mu;
+std::vector<void *> g_pinned_free;
+
+void *pinned_get() {
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        if (!g_pinned_free.empty()) {
+            void *p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, kPinnedBlock) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void pinned_put(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free.push_back(p);
+}
 
 // Internal stream ordered after the caller's stream; at destruction the caller's stream
 // is ordered after all internal work.
@@ -102,6 +172,11 @@ struct StreamScope {
     }
 };
 
+// Kernel launches issued by this host thread (a graph replay counts its kernels), read
+// by the entry points for pm_stats.kernel_launches.
+thread_local long long t_launches = 0;
+inline void note_launch(long long n = 1) { t_launches += n; }
+
 double now_s() {
     using namespace std::chrono;
     return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -120,6 +195,7 @@ struct Geometry {
     int per[3] = {1, 1, 1};
     int pax = -1;               // fixed-pressure axis, -1 if none
     long long N = 0;
+    const uint8_t *mask = nullptr;  // device copy of the mask (or the caller's device mask)
     uint8_t *flags = nullptr;   // device, one byte per cell (simple kernel)
     uint32_t *code = nullptr;   // device, one stencil code word per cell (tiled kernel)
 };
@@ -184,11 +260,14 @@ int build_geometry(const pm_domain *dom, cudaStream_t s, Scratch &scr, Geometry 
         PM_CK(cudaMemcpyAsync(m, dom->mask, (size_t)g.N, cudaMemcpyHostToDevice, s));
         dmask = m;
     }
+    g.mask = dmask;
     classify_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
                                                      g.pax, g.flags);
+    note_launch(1);
     PM_CK(cudaGetLastError());
     if ((st = scr.alloc(&g.code, (size_t)g.N))) return st;
     code_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.code);
+    note_launch(1);
     PM_CK(cudaGetLastError());
     return PM_OK;
 }
@@ -281,6 +360,123 @@ void percolation_host(const std::vector<uint8_t> &mask, int nx, int ny, int nz, 
     }
 }
 
+// Pore count and percolation of a device mask (pm_percolation.cuh): union-find of the
+// pore cells inside the box on the device, then a search with winding numbers on the
+// graph whose nodes are those components and whose edges are the pore pairs across the
+// periodic faces.  A loop in that graph with a nonzero winding along axis a is a fluid
+// path around the domain along a (the same criterion as percolation_host).  out[a] is
+// set for periodic axes only; check = false counts the pore cells only.
+int percolation_device(const Geometry &g, bool check, cudaStream_t s, Scratch &scr, long long *n_pore,
+                       int out[3]) {
+    const long long N = g.N;
+    out[0] = out[1] = out[2] = 0;
+    struct Info {
+        unsigned long long n_pore;
+        int wraps[3];
+        int overflow;
+        int err;
+        int pad;
+    };
+    if (N >= (long long)kNoLabel) {
+        // beyond 32-bit labels: host search on a copy of the mask
+        std::vector<uint8_t> hm((size_t)N);
+        PM_CK(cudaMemcpyAsync(hm.data(), g.mask, (size_t)N, cudaMemcpyDeviceToHost, s));
+        PM_CK(cudaStreamSynchronize(s));
+        long long c = 0;
+        for (uint8_t v : hm) c += v == 0;
+        *n_pore = c;
+        if (check && c > 0) percolation_host(hm, g.nx, g.ny, g.nz, g.per, out);
+        return PM_OK;
+    }
+    uint32_t *lab = nullptr;
+    Info *info = nullptr;
+    unsigned long long *table = nullptr;
+    int st;
+    if ((st = scr.alloc(&info, 1))) return st;
+    PM_CK(cudaMemsetAsync(info, 0, sizeof(Info), s));
+    if (check) {
+        if ((st = scr.alloc(&lab, (size_t)N)) || (st = scr.alloc(&table, (size_t)3 * kWrapSlots))) return st;
+        PM_CK(cudaMemsetAsync(table, 0xff, sizeof(unsigned long long) * 3 * kWrapSlots, s));
+        cc_init_kernel<<<launch_grid(N), 256, 0, s>>>(g.mask, N, lab, &info->n_pore);
+        cc_union_kernel<<<launch_grid(N), 256, 0, s>>>(g.nx, g.ny, g.nz, lab, &info->err);
+        cc_compress_kernel<<<launch_grid(N), 256, 0, s>>>(N, lab);
+        const long long faces = (long long)g.ny * g.nz + (long long)g.nx * g.nz + (long long)g.nx * g.ny;
+        cc_wrap_kernel<<<launch_grid(faces), 256, 0, s>>>(g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2], lab,
+                                                         info->wraps, table, &info->overflow);
+        note_launch(4);
+    } else {
+        count_pore_kernel<<<launch_grid(N), 256, 0, s>>>(g.mask, N, &info->n_pore);
+        note_launch();
+    }
+    PM_CK(cudaGetLastError());
+    Info h;
+    PM_CK(cudaMemcpyAsync(&h, info, sizeof(Info), cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaStreamSynchronize(s));
+    *n_pore = (long long)h.n_pore;
+    if (!check || h.n_pore == 0) return PM_OK;
+    if (h.err) return PM_ERR_CUDA;
+    if (h.overflow) {
+        // more distinct component pairs than the hash set holds: host search
+        std::vector<uint8_t> hm((size_t)N);
+        PM_CK(cudaMemcpyAsync(hm.data(), g.mask, (size_t)N, cudaMemcpyDeviceToHost, s));
+        PM_CK(cudaStreamSynchronize(s));
+        percolation_host(hm, g.nx, g.ny, g.nz, g.per, out);
+        return PM_OK;
+    }
+    for (int a = 0; a < 3; ++a) out[a] = h.wraps[a] != 0;
+    std::vector<unsigned long long> ht((size_t)3 * kWrapSlots);
+    PM_CK(cudaMemcpyAsync(ht.data(), table, sizeof(unsigned long long) * ht.size(), cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaStreamSynchronize(s));
+    // graph of components: edge A -> B crosses the periodic face of axis a in the + sense
+    std::unordered_map<uint32_t, int> id;
+    struct Edge {
+        int to, axis, sign;
+    };
+    std::vector<std::vector<Edge>> adj;
+    auto node = [&](uint32_t lbl) {
+        auto it = id.find(lbl);
+        if (it != id.end()) return it->second;
+        const int k = (int)adj.size();
+        id.emplace(lbl, k);
+        adj.emplace_back();
+        return k;
+    };
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < kWrapSlots; ++i) {
+            const unsigned long long key = ht[(size_t)a * kWrapSlots + i];
+            if (key == kWrapEmpty) continue;
+            const int A = node((uint32_t)(key >> 32)), B = node((uint32_t)(key & 0xffffffffu));
+            adj[(size_t)A].push_back({B, a, +1});
+            adj[(size_t)B].push_back({A, a, -1});
+        }
+    const size_t n = adj.size();
+    std::vector<std::array<long long, 3>> wind(n);
+    std::vector<uint8_t> seen(n, 0);
+    std::vector<int> queue;
+    for (size_t s0 = 0; s0 < n; ++s0) {
+        if (seen[s0]) continue;
+        seen[s0] = 1;
+        wind[s0] = {0, 0, 0};
+        queue.assign(1, (int)s0);
+        for (size_t h2 = 0; h2 < queue.size(); ++h2) {
+            const int c = queue[h2];
+            for (const Edge &e : adj[(size_t)c]) {
+                std::array<long long, 3> w = wind[(size_t)c];
+                w[e.axis] += e.sign;
+                if (!seen[(size_t)e.to]) {
+                    seen[(size_t)e.to] = 1;
+                    wind[(size_t)e.to] = w;
+                    queue.push_back(e.to);
+                } else {
+                    for (int k = 0; k < 3; ++k)
+                        if (wind[(size_t)e.to][k] != w[k]) out[k] = 1;
+                }
+            }
+        }
+    }
+    return PM_OK;
+}
+
 double time_step(const pm_options *o) {
     // 12 c2 dt^2 + (40 / Re) dt - 4 = 0: acoustic bound of the velocity-then-pressure
     // update (cell Laplacian eigenvalues <= 12) plus the viscous Gershgorin bound
@@ -324,12 +520,14 @@ struct Solver {
     int *active = nullptr;          // device, per problem
     int active_h[kMaxBatch] = {};
     long long total_units = 0;
+    double t_setup = 0.0;  // host seconds from the entry point to the first sweep
+    bool capturing = false;  // launches go into a graph (counted when it is replayed)
     const Geometry &G(int k) const { return multi ? *geo[k] : g; }
 
     Solver(const Geometry &gg, const pm_options &oo, cudaStream_t ss, Scratch &sc)
         : g(gg), o(oo), s(ss), scr(sc) {}
     ~Solver() {
-        if (hq) cudaFreeHost(hq);
+        pinned_put(hq);
     }
 
     dim3 block() const { return dim3(32, 8, 1); }
@@ -383,8 +581,12 @@ struct Solver {
         } else if ((st = scr.alloc(&partials, (size_t)(nprob * nblk_max * 4)))) {
             return st;
         }
-        if ((st = scr.alloc(&dq, (size_t)(nprob * 4)))) return st;
-        PM_CK(cudaMallocHost(&hq, sizeof(double) * nprob * 4));
+        // [nprob][4] window sums, then one slot for the device error flag (copied together)
+        if ((st = scr.alloc(&dq, (size_t)(nprob * 4 + 1)))) return st;
+        PM_CK(cudaMemsetAsync(dq, 0, sizeof(double) * (nprob * 4 + 1), s));
+        static_assert(sizeof(double) * kMaxBatch * 4 <= kPinnedBlock, "pinned block size");
+        hq = static_cast<double *>(pinned_get());
+        if (!hq) return PM_ERR_OOM;
         return PM_OK;
     }
 
@@ -393,6 +595,7 @@ struct Solver {
         if (u) PM_CK(cudaMemcpyAsync(F[k].u[F[k].cur], u, sizeof(T) * 3 * G(k).N, cudaMemcpyDeviceToDevice, s));
         if (p) PM_CK(cudaMemcpyAsync(F[k].p[F[k].cur], p, sizeof(T) * G(k).N, cudaMemcpyDeviceToDevice, s));
         sanitize_kernel<T><<<launch_grid(G(k).N), 256, 0, s>>>(G(k).flags, G(k).N, F[k].u[F[k].cur], F[k].p[F[k].cur]);
+        note_launch();
         PM_CK(cudaGetLastError());
         return PM_OK;
     }
@@ -442,6 +645,7 @@ struct Solver {
         B.multi = multi ? 1 : 0;
         B.active = multi ? active : nullptr;
         B.pres_axis = g.pax + 1;
+        B.err = err_flag();
         return B;
     }
 
@@ -476,8 +680,25 @@ struct Solver {
             reduce ? launch_simple<kModeP, true>(B, has_src) : launch_simple<kModeP, false>(B, has_src);
         }
         PM_CK(cudaGetLastError());
+        if (!capturing) note_launch();
         for (int k = 0; k < nprob; ++k) F[k].cur ^= 1;
         return PM_OK;
+    }
+
+    // device flag of the tiled kernel's bounded waits (the slot after the window sums)
+    int *err_flag() const { return dq ? reinterpret_cast<int *>(dq + 4 * nprob) : nullptr; }
+    // host copy of that flag as last brought back by reduce_to_host_async
+    bool err_seen() const {
+        int e = 0;
+        std::memcpy(&e, hq + 4 * nprob, sizeof(int));
+        return e != 0;
+    }
+    // synchronous read of the flag (paths without window reductions)
+    int check_err() {
+        int e = 0;
+        PM_CK(cudaMemcpyAsync(&e, err_flag(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        PM_CK(cudaStreamSynchronize(s));
+        return e ? PM_ERR_TIMEOUT : PM_OK;
     }
 
     long long reduce_blocks() const {
@@ -490,7 +711,8 @@ struct Solver {
         else
             reduce_partials_kernel<<<nprob, 256, 0, s>>>(partials, reduce_blocks(), g.N, dq);
         PM_CK(cudaGetLastError());
-        PM_CK(cudaMemcpyAsync(hq, dq, sizeof(double) * nprob * 4, cudaMemcpyDeviceToHost, s));
+        if (!capturing) note_launch();
+        PM_CK(cudaMemcpyAsync(hq, dq, sizeof(double) * (nprob * 4 + 1), cudaMemcpyDeviceToHost, s));
         return PM_OK;
     }
 
@@ -501,12 +723,15 @@ struct Solver {
     int tune(int reps = 2) {
         if (!use_tiled() || multi) return 0;
         static std::mutex mu;
-        static std::vector<std::array<long long, 6>> cache;  // nx, ny, nz, nprob, sizeof(T), zchunk
+        // device, nx, ny, nz, nprob, sizeof(T) -> zchunk
+        static std::vector<std::array<long long, 7>> cache;
+        const long long dev = current_device();
         {
             std::lock_guard<std::mutex> lock(mu);
             for (auto &c : cache)
-                if (c[0] == g.nx && c[1] == g.ny && c[2] == g.nz && c[3] == nprob && c[4] == (long long)sizeof(T)) {
-                    zchunk = (int)c[5];
+                if (c[0] == dev && c[1] == g.nx && c[2] == g.ny && c[3] == g.nz && c[4] == nprob &&
+                    c[5] == (long long)sizeof(T)) {
+                    zchunk = (int)c[6];
                     return 0;
                 }
         }
@@ -537,7 +762,7 @@ struct Solver {
         cudaEventDestroy(b);
         zchunk = best_zc;
         std::lock_guard<std::mutex> lock(mu);
-        cache.push_back({g.nx, g.ny, g.nz, nprob, (long long)sizeof(T), zchunk});
+        cache.push_back({dev, g.nx, g.ny, g.nz, nprob, (long long)sizeof(T), zchunk});
         return done;
     }
 
@@ -627,7 +852,9 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
         const int cur0 = S.F[0].cur;
         cudaError_t e = cudaStreamBeginCapture(S.s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            S.capturing = true;
             rc = S.window(M);
+            S.capturing = false;
             e = cudaStreamEndCapture(S.s, &graph);
             if (rc == PM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
             if (e != cudaSuccess || rc != PM_OK) {
@@ -650,6 +877,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
                 status = map_cuda(e);
                 break;
             }
+            note_launch(M + 1);
         } else if ((rc = S.window(M))) {
             status = rc;
             break;
@@ -665,6 +893,10 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
         win_ms += ms;
         win_sweeps += M;
         iters += M;
+        if (S.err_seen()) {
+            status = PM_ERR_TIMEOUT;
+            break;
+        }
         bool all = true, bad = false;
         for (int k = 0; k < S.nprob; ++k) {
             const double *q = S.hq + 4 * k;
@@ -718,6 +950,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
         else {
             cudaError_t e = cudaStreamSynchronize(S.s);
             if (e != cudaSuccess) status = map_cuda(e);
+            else if (S.err_seen()) status = PM_ERR_TIMEOUT;
         }
         if (st && status != PM_ERR_CUDA)
             for (int k = 0; k < S.nprob; ++k)
@@ -730,11 +963,14 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
             st[k].iters = (S.multi && conv_iter[k] >= 0) ? conv_iter[k] + 1 : iters;
             st[k].delta = mon[k].delta;
             st[k].err_est = mon[k].err;
-            st[k].sweep_ms = win_sweeps ? win_ms / (double)win_sweeps : 0.0;
-            st[k].sweeps_timed = win_sweeps;
+            bool src = false;
+            for (int q = 0; q < S.nprob; ++q) src |= S.src[q] != nullptr;
+            (src ? st[k].sweep_ms_src : st[k].sweep_ms) = win_sweeps ? win_ms / (double)win_sweeps : 0.0;
+            (src ? st[k].sweeps_timed_src : st[k].sweeps_timed) = win_sweeps;
             st[k].seconds = now_s() - t0;
             st[k].status = status;
             st[k].schedule = S.use_tiled() && !S.multi ? (S.zchunk > 0 ? S.zchunk : -1) : 0;
+            st[k].setup_seconds = S.t_setup;
         }
     return status;
 }
@@ -753,8 +989,8 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
     c1.stop_on_stall = true;
     int status = run_to_convergence<float>(S, st, t0, &c1);
     if (status != PM_OK && status != PM_ERR_NOT_CONVERGED) return status;
-    long long iters = st[0].iters, timed = st[0].sweeps_timed;
-    double ms = st[0].sweep_ms * (double)st[0].sweeps_timed;
+    long long iters = st[0].iters, timed = 0;
+    double ms = 0.0;
     float *r32[kMaxBatch] = {nullptr, nullptr, nullptr, nullptr};
     double q64[kMaxBatch][3];
     int rc;
@@ -767,6 +1003,7 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
             return rc;
         scale_copy_kernel<double, float><<<launch_grid(3 * N), 256, 0, S.s>>>(u64[k], S.F[k].u[S.F[k].cur], 1.0, 3 * N);
         scale_copy_kernel<double, float><<<launch_grid(N), 256, 0, S.s>>>(p64[k], S.F[k].p[S.F[k].cur], 1.0, N);
+        note_launch(2);
         for (int d = 0; d < 3; ++d) q64[k][d] = st[k].q[d];
     }
     PM_CK(cudaGetLastError());
@@ -786,6 +1023,7 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
             S.force[k] = 0.0;
             residual64_kernel<<<launch_grid(N), 256, 0, S.s>>>(g.flags, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
                                                                u64[k], p64[k], 1.0 / o.Re, f[0], f[1], f[2], r32[k]);
+            note_launch();
             for (int b = 0; b < 2; ++b) {
                 PM_CK(cudaMemsetAsync(S.F[k].u[b], 0, sizeof(float) * 3 * N, S.s));
                 PM_CK(cudaMemsetAsync(S.F[k].p[b], 0, sizeof(float) * N, S.s));
@@ -799,14 +1037,15 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
         status = run_to_convergence<float>(S, rs, t0, &c2);
         if (status != PM_OK && status != PM_ERR_NOT_CONVERGED) break;
         iters += rs[0].iters;
-        timed += rs[0].sweeps_timed;
-        ms += rs[0].sweep_ms * (double)rs[0].sweeps_timed;
+        timed += rs[0].sweeps_timed_src;
+        ms += rs[0].sweep_ms_src * (double)rs[0].sweeps_timed_src;
         double moved = 0.0;
         for (int k = 0; k < S.nprob; ++k) {
             accumulate_kernel<<<nb, 256, 0, S.s>>>(u64[k], p64[k], S.F[k].u[S.F[k].cur], S.F[k].p[S.F[k].cur], N,
                                                   part + (size_t)k * nb * 4);
         }
         reduce_partials_kernel<<<S.nprob, 256, 0, S.s>>>(part, nb, N, S.dq);
+        note_launch(S.nprob + 1);
         PM_CK(cudaGetLastError());
         PM_CK(cudaMemcpyAsync(S.hq, S.dq, sizeof(double) * S.nprob * 4, cudaMemcpyDeviceToHost, S.s));
         PM_CK(cudaStreamSynchronize(S.s));
@@ -834,8 +1073,8 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
         S.force[k] = force[k];
         for (int d = 0; d < 3; ++d) st[k].q[d] = q64[k][d];
         st[k].iters = iters;
-        st[k].sweeps_timed = timed;
-        st[k].sweep_ms = timed ? ms / (double)timed : 0.0;
+        st[k].sweeps_timed_src = timed;
+        st[k].sweep_ms_src = timed ? ms / (double)timed : 0.0;
         st[k].dc_rounds = rounds > o.dc_max_rounds ? o.dc_max_rounds : rounds;
         st[k].seconds = now_s() - t0;
         st[k].status = status;
@@ -862,7 +1101,7 @@ int iterate_impl(const pm_domain *dom, int dir, double drive, const pm_options *
     }
     PM_CK(cudaMemcpyAsync(u, S.F[0].u[S.F[0].cur], sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
     PM_CK(cudaMemcpyAsync(p, S.F[0].p[S.F[0].cur], sizeof(T) * g.N, cudaMemcpyDeviceToDevice, s));
-    return PM_OK;
+    return S.check_err();
 }
 
 // Solve a batch of drive directions on one geometry.  Fields stay on the device in
@@ -886,57 +1125,57 @@ inline int dc_dispatch(Solver<double> &, const Geometry &, pm_stats *, double, d
     return PM_ERR_UNSUPPORTED;
 }
 
-int count_fluid(const std::vector<uint8_t> &m) {
-    for (uint8_t v : m)
-        if (!v) return 1;
-    return 0;
-}
-
 template <typename T>
 int tensor_like(const pm_domain *dom, const pm_options *o, int ndirs, const int *dirs_in, double drive,
                        float *u_out, float *p_out, const float *u0, const float *p0, double kcols[3][3],
                        pm_stats *st, void *cuda_stream) {
     const double t0 = now_s();
-    std::vector<uint8_t> hm;
-    int rc = host_mask(dom, hm);
-    if (rc) return rc;
-    if (!count_fluid(hm)) return PM_ERR_NO_FLUID;
-    int per[3] = {dom->bc[0] == PM_BC_PERIODIC, dom->bc[1] == PM_BC_PERIODIC, dom->bc[2] == PM_BC_PERIODIC};
-    int perc[3] = {1, 1, 1};
+    const long long l0 = t_launches;
     const int pax = pressure_axis(dom);
     if (pax >= 0 && o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
-    if (o->check_percolation) {
-        percolation_host(hm, dom->nx, dom->ny, dom->nz, per, perc);
-        if (pax >= 0) perc[pax] = percolation_pressure(hm, dom->nx, dom->ny, dom->nz, per, pax);
-    }
-    int dirs[3], np = 0, slot[3] = {-1, -1, -1};
-    bool blocked = false;
-    for (int k = 0; k < ndirs; ++k) {
-        if (st) {
-            std::memset(&st[k], 0, sizeof(pm_stats));
-            st[k].percolates = perc[dirs_in[k]];
-        }
-        if (perc[dirs_in[k]]) {
-            slot[k] = np;
-            dirs[np++] = dirs_in[k];
-        } else
-            blocked = true;
-    }
     for (int k = 0; k < ndirs; ++k)
         for (int i = 0; i < 3; ++i) kcols[k][i] = 0.0;
     StreamScope ss(cuda_stream);
     if (ss.status) return ss.status;
-    int status = PM_OK;
+    int status = PM_OK, rc;
     pm_stats bst[kMaxBatch];
     std::memset(bst, 0, sizeof(bst));
+    int dirs[3], np = 0, slot[3] = {-1, -1, -1};
+    bool blocked = false;
     {
         Scratch scr(ss.s);
         Geometry g;
         if ((rc = build_geometry(dom, ss.s, scr, g))) return rc;
+        // pore count and percolation on the device (Sec. 5.1)
+        int perc[3] = {1, 1, 1}, wraps[3];
+        long long n_pore = 0;
+        if ((rc = percolation_device(g, o->check_percolation != 0, ss.s, scr, &n_pore, wraps))) return rc;
+        if (n_pore == 0) return PM_ERR_NO_FLUID;
+        if (o->check_percolation) {
+            for (int a = 0; a < 3; ++a) perc[a] = wraps[a];
+            if (pax >= 0) {
+                std::vector<uint8_t> hm;
+                if ((rc = host_mask(dom, hm))) return rc;
+                perc[pax] = percolation_pressure(hm, dom->nx, dom->ny, dom->nz, g.per, pax);
+            }
+        }
+        for (int k = 0; k < ndirs; ++k) {
+            if (st) {
+                std::memset(&st[k], 0, sizeof(pm_stats));
+                st[k].percolates = perc[dirs_in[k]];
+                st[k].n_fluid = n_pore;
+            }
+            if (perc[dirs_in[k]]) {
+                slot[k] = np;
+                dirs[np++] = dirs_in[k];
+            } else
+                blocked = true;
+        }
         if (np > 0) {
             Solver<T> S(g, *o, ss.s, scr);
             rc = S.init(np);
             if (rc) return rc;
+            S.t_setup = now_s() - t0;
             const double uscale = drive * dom->voxel_size * dom->voxel_size / (dom->viscosity * o->Re);
             const double pscale = drive * dom->voxel_size;
             for (int k = 0; k < np; ++k) {
@@ -994,10 +1233,13 @@ int tensor_like(const pm_domain *dom, const pm_options *o, int ndirs, const int 
             kcols[k][i] = sup * b.q[i] / o->Re * dom->voxel_size * dom->voxel_size;
         }
         if (st) {
-            int perc_k = st[k].percolates;
+            const int perc_k = st[k].percolates;
+            const long long nf = st[k].n_fluid;
             st[k] = b;
             st[k].percolates = perc_k;
+            st[k].n_fluid = nf;
         }
+        if (st) st[k].kernel_launches = t_launches - l0;
     }
     if (status == PM_OK && blocked) status = PM_ERR_NOT_PERCOLATING;
     return status;
@@ -1049,6 +1291,8 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
     uint32_t *code = reinterpret_cast<uint32_t *>(carve(4 * (size_t)N));
     T *u2 = reinterpret_cast<T *>(carve(3 * sizeof(T) * (size_t)N));
     T *p2 = reinterpret_cast<T *>(carve(sizeof(T) * (size_t)N));
+    int *err = reinterpret_cast<int *>(carve(sizeof(int)));
+    PM_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
     const int per[3] = {dom->bc[0] == PM_BC_PERIODIC, dom->bc[1] == PM_BC_PERIODIC, dom->bc[2] == PM_BC_PERIODIC};
     PM_CK(cudaMemcpyAsync(mask, dom->mask, (size_t)N, dom->mask_on_device ? cudaMemcpyDeviceToDevice
                                                                           : cudaMemcpyHostToDevice, s));
@@ -1071,6 +1315,7 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
     B.dt = (T)dts;
     B.dtc2 = (T)(dts * o->c2);
     B.nprob = 1;
+    B.err = err;
     for (int d = 0; d < 3; ++d) B.prob[0].f[d] = (T)(d == dir ? drive : 0.0);
     // ping-pong between the caller's fields (buffer 0) and the scratch (buffer 1)
     T *ub[2] = {u, u2}, *pb[2] = {p, p2};
@@ -1083,7 +1328,7 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
         B.prob[0].src = nullptr;
         B.prob[0].partials = nullptr;
         int st;
-        if (tiled_supported<T>(B.nx, B.ny, B.nz, 1)) {
+        if (o->kernel == 0 && tiled_supported<T>(B.nx, B.ny, B.nz, 1)) {
             if ((st = launch_tiled<T>(B, code, mode, false, false, o->schedule > 0 ? o->schedule : 0, s))) return st;
         } else {
             dim3 blk(32, 8, 1), grd((B.nx + 31) / 32, (B.ny + 7) / 8, (unsigned)B.nz);
@@ -1104,7 +1349,10 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
         PM_CK(cudaMemcpyAsync(u, u2, 3 * sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, s));
         PM_CK(cudaMemcpyAsync(p, p2, sizeof(T) * (size_t)N, cudaMemcpyDeviceToDevice, s));
     }
-    return PM_OK;
+    int e = 0;
+    PM_CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PM_CK(cudaStreamSynchronize(s));
+    return e ? PM_ERR_TIMEOUT : PM_OK;
 }
 
 // Adjoint sensitivity (differentiation pattern, not in the paper).  J = sum w_ij k_ij with
@@ -1116,6 +1364,12 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
     Geometry g;
     int rc = build_geometry(dom, s, scr, g);
     if (rc) return rc;
+    {
+        long long n_pore = 0;
+        int wraps[3];
+        if ((rc = percolation_device(g, false, s, scr, &n_pore, wraps))) return rc;
+        if (n_pore == 0) return PM_ERR_NO_FLUID;
+    }
     const T *alpha_t = nullptr;
     if (alpha) {
         if (sizeof(T) == sizeof(float)) {
@@ -1195,6 +1449,7 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
 template <typename T>
 int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_options *o, double *k_out,
                double *k_raw, pm_stats *st, cudaStream_t s, Scratch &scr, double t0) {
+    const long long l0 = t_launches;
     std::vector<Geometry> geos((size_t)nd);
     struct Prob {
         int d, j;
@@ -1206,20 +1461,20 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             k_out[9 * d + i] = 0.0;
             if (k_raw) k_raw[9 * d + i] = 0.0;
         }
-        std::vector<uint8_t> hm;
-        int rc = host_mask(&doms[d], hm);
+        int rc = build_geometry(&doms[d], s, scr, geos[(size_t)d]);
         if (rc) return rc;
-        if (!count_fluid(hm)) return PM_ERR_NO_FLUID;
-        const int per[3] = {doms[d].bc[0] == PM_BC_PERIODIC, doms[d].bc[1] == PM_BC_PERIODIC,
-                            doms[d].bc[2] == PM_BC_PERIODIC};
-        int perc[3] = {1, 1, 1};
-        if (o->check_percolation) percolation_host(hm, doms[d].nx, doms[d].ny, doms[d].nz, per, perc);
-        if ((rc = build_geometry(&doms[d], s, scr, geos[(size_t)d]))) return rc;
+        int perc[3] = {1, 1, 1}, wraps[3];
+        long long n_pore = 0;
+        if ((rc = percolation_device(geos[(size_t)d], o->check_percolation != 0, s, scr, &n_pore, wraps))) return rc;
+        if (n_pore == 0) return PM_ERR_NO_FLUID;
+        if (o->check_percolation)
+            for (int a = 0; a < 3; ++a) perc[a] = wraps[a];
         const int want = drives && drives[d] ? drives[d] : 7;
         for (int j = 0; j < 3; ++j) {
             if (st) {
                 std::memset(&st[3 * d + j], 0, sizeof(pm_stats));
                 st[3 * d + j].percolates = perc[j];
+                st[3 * d + j].n_fluid = n_pore;
             }
             if (!(want & (1 << j))) continue;
             if (!perc[j]) {
@@ -1240,6 +1495,7 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
         }
         int rc = S.init(np);
         if (rc) return rc;
+        S.t_setup = now_s() - t0;
         pm_stats bst[kMaxBatch];
         std::memset(bst, 0, sizeof(bst));
         rc = run_to_convergence<T>(S, bst, t0);
@@ -1256,11 +1512,15 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             }
             if (st) {
                 const int perc = st[3 * d + j].percolates;
+                const long long nf = st[3 * d + j].n_fluid;
                 st[3 * d + j] = bst[k];
                 st[3 * d + j].percolates = perc;
+                st[3 * d + j].n_fluid = nf;
             }
         }
     }
+    if (st)
+        for (int i = 0; i < 3 * nd; ++i) st[i].kernel_launches = t_launches - l0;
     return status;
 }
 
@@ -1305,6 +1565,15 @@ const char *pm_strerror(int s) {
 }
 
 int pm_version(void) { return kVersion; }
+
+int pm_release_memory(void) {
+    int dev = 0;
+    PM_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return PM_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pools[dev]) PM_CK(cudaMemPoolTrimTo(g_pools[dev], 0));
+    return PM_OK;
+}
 
 // Sec. 2: eigenvalues / eigenvectors of the symmetric part of k by cyclic Jacobi
 // rotations (each rotation zeroes one off-diagonal pair; sweeps until the off-diagonal
@@ -1495,6 +1764,8 @@ int pm_iterate_noalloc(const pm_domain *dom, int dir, double drive, const pm_opt
     if (o->precision == PM_FP32_DC64) return PM_ERR_INVALID_ARG;
     if (pressure_axis(dom) >= 0) return PM_ERR_UNSUPPORTED;
     if ((long long)dom->nx * dom->ny * dom->nz > kNoAllocMaxCells) return PM_ERR_TOO_LARGE;
+    // the caller's fields are one buffer of the ping-pong pair, read by 16-byte bulk copies
+    if (reinterpret_cast<uintptr_t>(u) % 16 || reinterpret_cast<uintptr_t>(p) % 16) return PM_ERR_INVALID_ARG;
     unsigned char *scr = nullptr;
     if ((st = noalloc_scratch(&scr))) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1535,9 +1806,6 @@ int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], 
     if (dJ_dalpha && !w) return PM_ERR_INVALID_ARG;
     if (o->precision == PM_FP32_DC64 || pressure_axis(dom) >= 0) return PM_ERR_UNSUPPORTED;
     const double t0 = now_s();
-    std::vector<uint8_t> hm;
-    if ((rc = host_mask(dom, hm))) return rc;
-    if (!count_fluid(hm)) return PM_ERR_NO_FLUID;
     StreamScope ss(cuda_stream);
     if (ss.status) return ss.status;
     {

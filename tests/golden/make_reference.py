@@ -28,7 +28,9 @@ def config1():
 def config2():
     # 256^3 periodic RSA pack, lognormal radii (median 10, sigma 0.3), porosity 0.38, seed 2
     m, _ = G.rsa_sphere_pack((256, 256, 256), 10.0, 0.3, 4.0, 25.0, 0.38, seed=2)
-    return m, (0, 1, 2), 1e-8
+    # the off-diagonals are ~1e-3 of the diagonal: a per-component check at 1e-5 needs the
+    # reference's remaining change far below 1e-8 of the driven component
+    return m, (0, 1, 2), 1e-10
 
 
 CONFIGS = {"config1": config1, "config2": config2}

@@ -9,9 +9,14 @@ Tolerances (derived from the arithmetic):
   value differs by a few ulp per iteration -> 1e-11 relative to the field's max.
 * FP32 fields: one FP32 rounding per operation, ~30 operations per update, errors do
   not grow within a few iterations -> 2e-5 relative to the field's max.
-* Converged k: the BASELINE target, 1e-5 relative per component, with off-diagonal
-  components compared against 1e-5 x max |k_ii| (they are differences of near-equal
-  fluxes and carry the diagonal's absolute error).
+* Converged k, forms with FP64 accuracy (FP64 fields, FP32 sweeps + FP64 defect
+  correction): every k_ij within its tolerance of its own oracle value, off-diagonal
+  components included.
+* Converged k, plain FP32 sweeps: the iteration stalls at the FP32 floor, about 1e-7 of
+  the driven component's mean velocity; an off-diagonal component (1e-3 .. 1e-2 of the
+  diagonal on these packs) carries that absolute error, so it is held to 1e-5 x max
+  |k_ii| and the diagonal to 1e-5 of its own value.  Meeting 1e-5 on each off-diagonal
+  needs the defect correction.
 """
 import numpy as np
 import pytest
@@ -121,6 +126,8 @@ def test_config1_kxx_converged(api, config1, config1_oracle, precision, tol, rel
     ko = config1_oracle
     assert k[0] == pytest.approx(ko[0], rel=rel)
     np.testing.assert_allclose(k[1:], ko[1:], rtol=0, atol=rel * abs(ko[0]))
+    if precision == "fp64":
+        np.testing.assert_allclose(k, ko, rtol=1e-6)  # each component against its own value
     # returned fields: Darcy-scaled (drive = dx = mu = 1 -> mean u_x = k_xx)
     u = r["u"].double()
     assert float(u[0].mean()) == pytest.approx(k[0], rel=1e-6)
@@ -136,6 +143,8 @@ def test_full_tensor_batched(api, oracle_mod):
         np.testing.assert_allclose(r["k_raw"], k_raw_o, rtol=0, atol=rel * scale)
         np.testing.assert_allclose(r["k"], k_sym_o, rtol=0, atol=rel * scale)
         np.testing.assert_allclose(np.diag(r["k"]), np.diag(k_sym_o), rtol=rel)
+        if prec == "fp64":
+            np.testing.assert_allclose(r["k_raw"], k_raw_o, rtol=1e-6)  # each against its own value
 
 
 def test_non_percolating_axis(api):
@@ -191,6 +200,7 @@ def test_defect_correction_config1(api, config1, config1_oracle):
     k, ko = r["k_col"], config1_oracle
     assert k[0] == pytest.approx(ko[0], rel=1e-8)
     np.testing.assert_allclose(k[1:], ko[1:], rtol=0, atol=1e-8 * abs(ko[0]))
+    np.testing.assert_allclose(k, ko, rtol=1e-6)  # each component against its own value
 
 
 def test_defect_correction_full_tensor(api, oracle_mod):
@@ -200,6 +210,7 @@ def test_defect_correction_full_tensor(api, oracle_mod):
     assert r["status"] == api.PM_OK
     scale = np.abs(np.diag(k_raw_o)).max()
     np.testing.assert_allclose(r["k_raw"], k_raw_o, rtol=0, atol=1e-8 * scale)
+    np.testing.assert_allclose(r["k_raw"], k_raw_o, rtol=1e-6)  # each component against its own value
 
 
 @pytest.mark.slow
@@ -269,3 +280,60 @@ def test_defect_correction_on_a_slowly_converging_geometry(api):
     rdc = api.solve_direction(d, 0, fields=False, precision="dc64", tol=1e-9, check_every=100)
     assert r64["status"] == api.PM_OK and rdc["status"] == api.PM_OK
     assert rdc["k_col"][0] == pytest.approx(r64["k_col"][0], rel=1e-7)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("drive_dir", [0, 2])
+def test_config2_full_size_fields_after_21_iterations(api, oracle_mod, drive_dir):
+    """256^3 benchmark geometry in the benchmark's work split (chunks of 64 planes): the
+    FP32 fields after 21 iterations match the oracle's element by element."""
+    mask, _ = G.rsa_sphere_pack((256, 256, 256), 10.0, 0.3, 4.0, 25.0, 0.38, seed=2)
+    Ug, pg = _gpu_iterate(api, mask, 21, drive_dir, "fp32", schedule=64)
+    Uo, po = _oracle_iterate(oracle_mod, mask, 21, drive_dir, dt=api.time_step())
+    np.testing.assert_allclose(Ug, Uo, rtol=0, atol=2e-5 * np.abs(Uo).max())
+    np.testing.assert_allclose(pg, po, rtol=0, atol=2e-5 * np.abs(po).max())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_persistent_rounds_trajectory(api, oracle_mod, precision):
+    """1024 x 640 x 6 cells make 16 x 54 = 864 tile columns, more than the persistent
+    grid (2 CTAs per SM for FP32, 1 for FP64): whole-column rounds in lockstep run
+    before the equal plane ranges of the remaining columns.  Element-wise parity with
+    the oracle after 1, 2 and 10 iterations."""
+    mask = G.random_blocks((6, 640, 1024), 0.3, seed=41)
+    dt = api.time_step()
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    for n in (1, 2, 10):
+        for drive_dir in (0, 1):
+            Ug, pg = _gpu_iterate(api, mask, n, drive_dir, precision, schedule=-1)
+            Uo, po = _oracle_iterate(oracle_mod, mask, n, drive_dir, dt=dt)
+            np.testing.assert_allclose(Ug, Uo, rtol=0, atol=tol * np.abs(Uo).max(), err_msg=f"u n={n}")
+            np.testing.assert_allclose(pg, po, rtol=0, atol=tol * np.abs(po).max(), err_msg=f"p n={n}")
+
+
+@pytest.mark.slow
+def test_beyond_2_31_cells_replicates_the_unit_cell(api, oracle_mod):
+    """A periodic 64^3 cell (checked against the oracle) tiled 21 x 21 x 19 times gives
+    1344 x 1344 x 1216 = 2.2e9 cells, beyond 32-bit cell indices.  Every cell does the
+    same arithmetic as its image in the unit cell, so after 10 FP32 iterations each
+    replica of the large fields is bit-identical to the unit cell's fields."""
+    cell = G.overlapping_spheres((64, 64, 64), 4.0, 0.6, seed=51)
+    n = 10
+    u1, p1 = _gpu_iterate(api, cell, n, 0, "fp32")
+    Uo, po = _oracle_iterate(oracle_mod, cell, n, 0, dt=api.time_step())
+    np.testing.assert_allclose(u1, Uo, rtol=0, atol=2e-5 * np.abs(Uo).max())
+    reps = (19, 21, 21)
+    big = torch.from_numpy(cell).cuda().repeat(reps)
+    assert big.numel() > 2 ** 31
+    u = torch.zeros((3,) + tuple(big.shape), dtype=torch.float32, device="cuda")
+    p = torch.zeros(tuple(big.shape), dtype=torch.float32, device="cuda")
+    api.iterate(big, u, p, n, drive_dir=0, precision="fp32")
+    torch.cuda.synchronize()
+    del big
+    ref_u = torch.from_numpy(u1).float().cuda()
+    ref_p = torch.from_numpy(p1).float().cuda()
+    for d in range(3):
+        v = u[d].view(19, 64, 21, 64, 21, 64)
+        assert bool((v == ref_u[d][None, :, None, :, None, :]).all()), d
+    v = p.view(19, 64, 21, 64, 21, 64)
+    assert bool((v == ref_p[None, :, None, :, None, :]).all())
