@@ -1,13 +1,10 @@
 // Tiled z-marching fused sweep.
 //
 // A CTA owns a TX x TY column tile of the (x, y) plane and marches along z over a chunk
-// of planes.  Each plane of the three velocity arrays is copied with its 2-voxel halo into
-// a 7-stage shared-memory ring by bulk asynchronous copies (one copy per contiguous run of
-// a box row, issued by 46 threads, completion counted in bytes on the stage's mbarrier),
-// four planes ahead of use, so each velocity value comes from DRAM once per sweep and the
-// neighbour reuse is served by shared memory (x, y) and per-thread register queues (z).
-// The input pressure and the stencil codes are needed at the thread's own cells only and
-// go straight from global memory into registers, one step ahead of use.
+// of planes.  Each plane of the five input arrays (u_x, u_y, u_z, p, stencil code) is
+// copied with its 2-voxel halo into a 5-stage shared-memory ring by cp.async, two planes
+// ahead of use, so each field value comes from DRAM once per sweep and the neighbour
+// reuse is served by shared memory (x, y) and per-thread register queues (z).
 //
 // Per step t the CTA
 //   reads plane t of its own column into the z queues,
@@ -81,45 +78,22 @@ __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, in
     }
 }
 
-// ------------------------------------------------------------------ async copy helpers
-// Bulk asynchronous copies global -> shared memory (cp.async.bulk) whose completion is
-// counted in bytes on an mbarrier of the ring stage they fill.
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+// ------------------------------------------------------------------ cp.async helpers
+// 16-byte asynchronous global -> shared copies (L2 only: the tile is staged in shared
+// memory, nothing is reused from L1).
+__device__ __forceinline__ void cp_async16(void *s, const void *g) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
 }
-// one arrival that also announces the bytes the stage's copies will deliver
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+// zero-filling form: src_bytes = 0 reads nothing and writes 16 zero bytes
+__device__ __forceinline__ void cp_async16z(void *s, const void *g, unsigned src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(g), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of the given parity (each try_wait suspends the thread for
-// a hardware-defined time slice): false once the bound has run out.
-constexpr int kWaitTries = 1 << 20;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int i = 0; i < kWaitTries; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-// the initialised barriers become visible to the copy engine
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // ------------------------------------------------------------------ kernel
@@ -128,30 +102,28 @@ __device__ __forceinline__ void fence_barrier_init() {
 // x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4 high (y0 - 2 .. y0 + TY + 1); the
 // stencil needs +-2 in x and y.
 constexpr int kTX = 64, kTY = 12, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY;
-// Ring of kStages planes of the three velocity arrays: planes t-2, t-1, t are read in step
-// t while the copies of the next kAhead planes are in flight.
-constexpr int kStages = 7, kAhead = kStages - 3;
-// p^n is needed on box rows 2 .. kTY + 2 (tile rows and the +y halo row), u_y on rows
-// 1 .. kTY + 2, u_x and u_z on all rows
+// Ring of kStages planes: planes t-2, t-1, t are read in step t while the copies of the
+// next kAhead planes are in flight.
+constexpr int kStages = 5, kAhead = kStages - 3;
+// p^n, the input pressure and the stencil codes are needed on box rows 2 .. kTY + 2 (tile
+// rows and the +y halo row) only, u_y on rows 1 .. kTY + 2; u_x and u_z on all rows
 constexpr int kPNL = (kTY + 1) * kBX, kPNo = 2 * kBX;
 constexpr int kUYL = (kTY + 2) * kBX, kUYo = kBX;
-// box rows copied per plane: u_x and u_z kBY each, u_y kTY + 2; one copying thread per row
-constexpr int kRows = 2 * kBY + kTY + 2;
-// runs of whole 16-byte chunks in a box row (the periodic wrap splits a row)
-constexpr int kMaxRuns = kBX / 4;
 // CTAs per SM the FP32 kernel is built for (registers and shared memory)
 constexpr int kMinBlocks = 2;
 constexpr int kNT = (kTX / 2) * kTY;
-static_assert(kRows <= kNT, "one thread per copied row");
 
-// One ring stage: the three velocity arrays of one plane, contiguous, so that every access
-// is a per-step stage pointer plus a compile-time offset.  u_y starts at box row 1
-// (index = box index - kUYo).
+// One ring stage: the five arrays of one plane, contiguous, so that every access is a
+// per-step stage pointer plus a compile-time offset.  Arrays that need fewer box rows
+// start at a later row: u_y at row 1 (index = box index - kUYo), p and the codes at
+// row 2 (index = box index - kPNo).
 template <typename T>
 struct TiledStage {
     T ux[kPL];
     T uz[kPL];
     T uy[kUYL];
+    T pin[kPNL];
+    uint32_t cd[kPNL];
 };
 
 // Wall coefficients per wall kind.  Non-fluid nodes hold 0, so with S = u(-1) + u(+1)
@@ -166,24 +138,12 @@ struct alignas(2 * sizeof(T)) WallCoef {
     T A, K;
 };
 
-// A run of a box row: box cells [dst, dst + len) come from global x = src .. src + len - 1
-// of the row, or from the zero row (src < 0: outside a wall).
-struct CopyRun {
-    int dst, src, len;
-};
-
 template <typename T>
-struct alignas(128) TiledSmem {
+struct TiledSmem {
     TiledStage<T> st[kStages];
     T pn[2][kPNL];  // index: box index - 2 kBX
     WallCoef<T> coef[4];
-    unsigned long long full[kStages];  // mbarrier per ring stage
-    CopyRun runs[kMaxRuns];
-    int nruns;
 };
-
-// Zero source for box rows and runs that lie outside a wall (one FP64 box row).
-static __device__ __align__(128) unsigned char g_zero_row[kBX * sizeof(double)];
 
 // A pair of x-adjacent values (aligned for one 2-wide shared-memory access).
 template <typename T>
@@ -194,20 +154,9 @@ template <typename T>
 __device__ __forceinline__ Pair<T> ld2(const T *p) {
     return *reinterpret_cast<const Pair<T> *>(p);
 }
-// read-only global pair (input pressure, stencil codes)
 template <typename T>
-__device__ __forceinline__ Pair<T> ldg2(const T *p) {
-    if constexpr (sizeof(T) == 4) {
-        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-        return Pair<T>{v.x, v.y};
-    } else {
-        const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
-        return Pair<T>{v.x, v.y};
-    }
-}
-__device__ __forceinline__ Pair<uint32_t> ldg2u(const uint32_t *p) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-    return Pair<uint32_t>{v.x, v.y};
+__device__ __forceinline__ Pair<uint32_t> ld2u(const uint32_t *p) {
+    return *reinterpret_cast<const Pair<uint32_t> *>(p);
 }
 
 // Byte offset of the coefficient-table entry of the wall kind at bit sh of word c (one
@@ -224,7 +173,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int tiles_x, int tiles_y,
                        long long per_cta, int zchunk) {
     // single geometry: B.nx.. and the arguments; multi-geometry: per problem (below)
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     TiledSmem<T> &S = *reinterpret_cast<TiledSmem<T> *>(smem_raw);
     int nx = B.nx, ny = B.ny, nz = B.nz;
     long long N = B.N, plane = (long long)nx * ny;
@@ -249,7 +198,6 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         tiles_y = B.prob[mp].tiles_y;
     }
 
-    const uint32_t st_base = smem_u32(&S.st[0]), full_base = smem_u32(&S.full[0]);
     if (tid < 4) {
         // Appendix B: kind 0 case 6, kind 1 case 1, kind 2 cases 4/5, kind 3 cases 2/3
         const int kind = tid;
@@ -258,13 +206,6 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         w.K = kind == 2 ? T(-1) : T(0);
         S.coef[tid] = w;
     }
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(full_base + 8u * s, 1u);
-        fence_barrier_init();
-    }
-    uint32_t phase = 0;    // bit s: parity of the next phase of stage s
-    uint32_t pending = 0;  // bit s: copies issued into stage s and not waited for
-    bool failed = false;
 
     // Persistent CTAs over columns (a column = one drive on one x-y tile, all planes).
     // Phase 1: rounds in which CTA b marches whole column r G + b, so that all CTAs are at
@@ -310,67 +251,67 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     const int rs = B.multi ? 0 : pi;  // slot of red_sum
     const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
     const SweepProblem<T> &P = B.prob[pi];
+    const T *__restrict__ gux = P.uin;
+    const T *__restrict__ guy = P.uin + N;
+    const T *__restrict__ guz = P.uin + 2 * N;
     const T *__restrict__ gp = P.pin;
 
-    // Copy plan.  Thread r < kRows copies box row r of the three velocity arrays (u_x rows
-    // 0..kBY-1, u_z rows 0..kBY-1, u_y rows 1..kTY+2) of every plane with one bulk copy per
-    // run of the row; the runs (chunk starts are multiples of 4 cells, nx % 4 == 0, so a
-    // chunk wraps around a periodic boundary as a whole) are the same for every row.
-    if (tid == 0) {
-        int n = 0;
-        for (int j = 0; j < kBX / 4; ++j) {
-            const int gx = nb_coord(x0 - 4 + 4 * j, nx, B.per[0]);
-            if (n > 0 && ((S.runs[n - 1].src < 0 && gx < 0) ||
-                          (S.runs[n - 1].src >= 0 && gx == S.runs[n - 1].src + S.runs[n - 1].len))) {
-                S.runs[n - 1].len += 4;
-            } else {
-                S.runs[n] = CopyRun{4 * j, gx, 4};
-                ++n;
-            }
+    // Copy plan.  Field boxes are kBY rows of FCH 16-byte chunks, the code box kBY rows
+    // of CCH chunks; chunk starts are multiples of 4 cells (nx % 4 == 0), so a chunk
+    // wraps around a periodic boundary as a whole.  fo / co: in-plane element offset of
+    // this thread's field / code chunk (-1: none or outside a wall), fs / cs: its place
+    // in the box.
+    constexpr int FE = 16 / (int)sizeof(T), FCH = kBX / FE, CCH = kBX / 4;
+    constexpr int FR = (FCH * kBY + kNT - 1) / kNT;
+    int fo[FR], fs[FR];
+    bool fhas[FR], fuy[FR], fp[FR];  // chunk exists / row also holds u_y / also p
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+        const int c = tid + r * kNT;
+        fo[r] = -1;
+        fs[r] = 0;
+        fhas[r] = c < FCH * kBY;
+        fuy[r] = fp[r] = false;
+        if (fhas[r]) {
+            const int hy = c / FCH, hx = (c % FCH) * FE;
+            fs[r] = hy * kBX + hx;
+            fuy[r] = hy >= 1 && hy <= kTY + 2;
+            fp[r] = hy >= 2 && hy <= kTY + 2;
+            const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
+            if (gx >= 0 && gy >= 0) fo[r] = gx + nx * gy;
         }
-        S.nruns = n;
     }
-    const T *row_src = nullptr;  // global row of this thread's copy (plane 0), nullptr outside a wall
-    uint32_t row_dst = 0;        // its byte offset in a stage
-    if (tid < kRows) {
-        int arr, hy;
-        if (tid < kBY) {
-            arr = 0;
-            hy = tid;
-            row_dst = (uint32_t)(sizeof(T) * (hy * kBX));
-        } else if (tid < 2 * kBY) {
-            arr = 2;
-            hy = tid - kBY;
-            row_dst = (uint32_t)(sizeof(T) * (kPL + hy * kBX));
-        } else {
-            arr = 1;
-            hy = tid - 2 * kBY + 1;
-            row_dst = (uint32_t)(sizeof(T) * (2 * kPL + (hy - 1) * kBX));
-        }
-        const int gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
-        if (gy >= 0) row_src = P.uin + (long long)arr * N + (long long)gy * nx;
+    // code chunks: box rows 2 .. kTY + 2; cs is the index in the stage's code array
+    int co = -1, cs = 0;
+    const bool chas = tid < CCH * (kTY + 1);
+    if (chas) {
+        const int hy = 2 + tid / CCH, hx = (tid % CCH) * 4;
+        cs = hy * kBX + hx - kPNo;
+        const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
+        if (gx >= 0 && gy >= 0) co = gx + nx * gy;
     }
-    const T *zero_row = reinterpret_cast<const T *>(g_zero_row);
-    __syncthreads();  // runs table ready; the ring is free
-    const int nruns = S.nruns;
     auto issue_plane = [&](int k, int slot) {
-        const uint32_t bar = full_base + 8u * slot;
-        pending |= 1u << slot;
-        if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)sizeof(TiledStage<T>));
-        if (tid < kRows) {
-            const uint32_t dst = st_base + (uint32_t)sizeof(TiledStage<T>) * slot + row_dst;
-            const int gz = nb_coord(k, nz, B.per[2]);
-            if (gz < 0 || !row_src) {
-                bulk_g2s(dst, zero_row, (uint32_t)(kBX * sizeof(T)), bar);
-            } else {
-                const T *src = row_src + (long long)gz * plane;
-                for (int q = 0; q < nruns; ++q) {
-                    const CopyRun r = S.runs[q];
-                    bulk_g2s(dst + (uint32_t)(sizeof(T) * r.dst), r.src >= 0 ? src + r.src : zero_row,
-                             (uint32_t)(sizeof(T) * r.len), bar);
-                }
-            }
+        TiledStage<T> &G = S.st[slot];
+        const int gz = nb_coord(k, nz, B.per[2]);
+        const long long po = (long long)gz * plane;
+#pragma unroll
+        for (int r = 0; r < FR; ++r) {
+            if (!fhas[r]) continue;
+            const int e = fs[r];
+            // outside a wall: the zero-filling copy reads nothing (a valid address is given)
+            const bool in = gz >= 0 && fo[r] >= 0;
+            const long long o = in ? po + fo[r] : 0;
+            const unsigned nb = in ? 16u : 0u;
+            cp_async16z(&G.ux[e], gux + o, nb);
+            cp_async16z(&G.uz[e], guz + o, nb);
+            if (fuy[r]) cp_async16z(&G.uy[e - kUYo], guy + o, nb);
+            if (fp[r]) cp_async16z(&G.pin[e - kPNo], gp + o, nb);
         }
+        if (chas) {
+            const bool in = gz >= 0 && co >= 0;
+            cp_async16z(&G.cd[cs], code + (in ? po + co : 0), in ? 16u : 0u);
+        }
+        cp_async_commit();
     };
 
     const int own = (ty + 2) * kBX + 4 + 2 * lane;  // box index of the first cell of the pair
@@ -385,11 +326,12 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         if (wx >= 0 && wy >= 0) gin_wrap = (long long)wx + (long long)nx * wy;
     }
     // halo p^n: the last warp takes the row y0 + TY (pairs), the last TY lanes of the
-    // warp before it the column x0 + TX (single cells)
+    // warp before it the column x0 + TX (single cells); for FP32 these lanes issue no
+    // copies (288 chunks per array), which balances the work before the barrier
     const bool hrow = ty == kTY - 1, hcol = ty == kTY - 2 && lane >= 32 - kTY;
     const int hown = hrow ? (kTY + 2) * kBX + 4 + 2 * lane : (lane - (32 - kTY) + 2) * kBX + kTX + 4;
-    long long hg = -1;  // global in-plane index of the halo cell (pair), -1 outside a wall
-    if (hrow || hcol) {
+    long long hg = -1;
+    if ((hrow || hcol) && SRC) {
         const int gx = nb_coord(x0 + (hown % kBX) - 4, nx, B.per[0]), gy = nb_coord(y0 + hown / kBX - 2, ny, B.per[1]);
         if (gx >= 0 && gy >= 0) hg = (long long)gx + (long long)nx * gy;
     }
@@ -398,23 +340,6 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     const int wxp = nb_coord(gx_own + 2, nx, B.per[0]), wyp = nb_coord(gy_own + 1, ny, B.per[1]);
     const long long ex1_off = wxp >= 0 ? (long long)wxp - (gx_own + 1) : 0;  // second cell's +x
     const long long ey_off = wyp >= 0 ? ((long long)wyp - gy_own) * nx : 0;
-
-    // per-cell inputs straight from global memory into registers, one step ahead of use:
-    // the input pressure of the plane whose p^n is formed next, and the stencil codes of
-    // the plane updated next (plane k outside a wall: 0)
-    auto load_pin = [&](int k) -> Pair<T> {
-        const int gz = nb_coord(k, nz, B.per[2]);
-        return (gz >= 0 && gin_wrap >= 0) ? ldg2(gp + (long long)gz * plane + gin_wrap) : Pair<T>{T(0), T(0)};
-    };
-    auto load_hpin = [&](int k) -> Pair<T> {
-        const int gz = nb_coord(k, nz, B.per[2]);
-        if (gz < 0 || hg < 0) return Pair<T>{T(0), T(0)};
-        if (hrow) return ldg2(gp + (long long)gz * plane + hg);
-        return Pair<T>{__ldg(gp + (long long)gz * plane + hg), T(0)};
-    };
-    auto load_code = [&](int k) -> Pair<uint32_t> {
-        return (k >= m0 && k < m1 && real0) ? ldg2u(code + (long long)k * plane + gin_own) : Pair<uint32_t>{0u, 0u};
-    };
 
     Pair<T> qx[5], qy[5], qz[5];
 #pragma unroll
@@ -425,28 +350,27 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 
     const int t0 = m0 - 2;
-    const int tend = m1 + 1;
     int s2 = ((t0 - 2) % kStages + kStages) % kStages;  // ring stages of planes t-2, t-1, t
     int s1 = (s2 + 1) % kStages, s0 = (s2 + 2) % kStages;
     {
         int sl = s0;
-        for (int k = 0; k < kAhead && t0 + k <= tend; ++k) {
+        for (int k = 0; k < kAhead; ++k) {
             issue_plane(t0 + k, sl);
             sl = sl == kStages - 1 ? 0 : sl + 1;
         }
     }
-    Pair<T> pin_n = load_pin(t0 - 1), hpin_n = load_hpin(t0 - 1);
-    Pair<uint32_t> code_n = load_code(t0 - 2);
 
-    // p^n of one cell at box position e of plane k (stage K, the plane below in KM)
-    auto press1 = [&](const TiledStage<T> &K, const TiledStage<T> &KM, int e, int k, long long g, T p0) -> T {
+    // p^n of one cell at box position e of plane k (stage K), the plane below in KM
+    auto press1 = [&](const TiledStage<T> &K, const TiledStage<T> &KM, int e, int k, long long g) -> T {
         const T dv = (K.ux[e] - K.ux[e - 1]) + (K.uy[e - kUYo] - K.uy[e - kBX - kUYo]) + (K.uz[e] - KM.uz[e]);
         T rp = T(0);
         if (SRC && g >= 0) {
             const int gz = nb_coord(k, nz, B.per[2]);
             if (gz >= 0) rp = P.src[3 * N + (long long)gz * plane + g];
         }
-        return MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
+        const T p0 = K.pin[e - kPNo];
+        const T pn = MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
+        return (K.cd[e - kPNo] & 1u) ? pn : T(0);
     };
     // second derivative across the flow (Appendix B) from the 3-bit wall code, added to lap
     auto perp = [&](T &lap, uint32_t cc, int sh, T um2, T um1, T u0, T up1, T up2) {
@@ -459,41 +383,30 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
 
     T *outx = P.uout + (long long)m0 * plane + gin_own;
     T *outp = P.pout + (long long)m0 * plane + gin_own;
+    const int tend = m1 + 1;
     // one plane step; kRot = step index mod 5.  The z queues are circular with compile-time
     // slots, so advancing them moves no registers: after this step's load, queue entry k
     // (u_x, u_y: planes m-2 .. m+2 of the updated plane m = t-2; u_z: planes m-1 .. m+1 as
     // entries 0 .. 2) lives in slot (kRot + 1 + k) % 5.  The loop below unrolls five steps.
-    // Returns false when the data of plane t did not arrive within the wait bound.
-    auto step = [&](auto Rc, int t) -> bool {
+    auto step = [&](auto Rc, int t) {
         constexpr int kRot = decltype(Rc)::value;
-        const bool ok = mbar_wait(full_base + 8u * s0, (phase >> s0) & 1u);
-        if (ok) {
-            phase ^= 1u << s0;
-            pending &= ~(1u << s0);
-        }
-        // every thread has its plane; the stage of plane t - 3 and p^n of plane t - 3 are
-        // no longer read; p^n of plane t - 2 is published
-        if (__syncthreads_or(!ok)) return false;
-        if (t + kAhead <= tend) {
+        cp_async_wait<kAhead - 1>();
+        __syncthreads();
+        {
             int sl = s0 + kAhead;
             if (sl >= kStages) sl -= kStages;
             issue_plane(t + kAhead, sl);
         }
-        const Pair<T> pin = pin_n, hpin = hpin_n;
-        const Pair<uint32_t> c = code_n;
-        pin_n = load_pin(t);
-        hpin_n = load_hpin(t);
-        code_n = load_code(t - 1);
         const TiledStage<T> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
         // z queues of the own column pair
         qx[kRot % 5] = ld2(&G0.ux[own]);
         qy[kRot % 5] = ld2(&G0.uy[own - kUYo]);
         qz[(kRot + 3) % 5] = ld2(&G1.uz[own]);
-        // own p^n on plane t-1 (kept in registers until after the update of plane t-2); a
-        // solid cell has zero divergence (its six faces are non-fluid) and p = 0, so it
-        // keeps p = 0 without a test
+        // own p^n on plane t-1 (kept in registers until after the update of plane t-2)
         Pair<T> pn_new;
         {
+            const Pair<uint32_t> cd = ld2u<T>(&G1.cd[own - kPNo]);
+            const Pair<T> pin = ld2(&G1.pin[own - kPNo]);
             const Pair<T> uyd = ld2(&G1.uy[own - kBX - kUYo]);
             const T uxl = G1.ux[own - 1];
             T dv0 = (qx[(kRot + 1 + 3) % 5].a - uxl) + (qy[(kRot + 1 + 3) % 5].a - uyd.a) + (qz[(kRot + 1 + 2) % 5].a - qz[(kRot + 1 + 1) % 5].a);
@@ -507,10 +420,14 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                     rp1 = r.b;
                 }
             }
-            pn_new.a = MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0);
-            pn_new.b = MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1);
-            if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU)
+            const bool pore0 = cd.a & 1u, pore1 = cd.b & 1u;
+            pn_new.a = pore0 ? (MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0)) : T(0);
+            pn_new.b = pore1 ? (MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1)) : T(0);
+            if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) {
+                dv0 = pore0 ? dv0 : T(0);
+                dv1 = pore1 ? dv1 : T(0);
                 acc[3] += (double)dv0 * (double)dv0 + (double)dv1 * (double)dv1;
+            }
         }
         const int m = t - 2;
         if (m >= m0 && real0) {
@@ -521,6 +438,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 uy_n = qy[(kRot + 1 + 2) % 5];
                 uz_n = qz[(kRot + 1 + 1) % 5];
             } else {
+                const Pair<uint32_t> c = ld2u<T>(&G2.cd[own - kPNo]);
                 const T *PN = S.pn[m & 1];  // index: box index - 2 kBX
                 const T *ux = G2.ux, *uy = G2.uy, *uz = G2.uz;
                 const long long gidx = (long long)m * plane + gin_own;
@@ -623,6 +541,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own - 2 * kBX]) = pn_new;
         if (hrow) {
             // the +y halo row as pairs (same arithmetic as press1, 2-wide loads)
+            const Pair<uint32_t> hc = ld2u<T>(&G1.cd[hown - kPNo]);
+            const Pair<T> hp = ld2(&G1.pin[hown - kPNo]);
             const Pair<T> hux = ld2(&G1.ux[hown]);
             const T huxl = G1.ux[hown - 1];
             const Pair<T> huy = ld2(&G1.uy[hown - kUYo]), huyd = ld2(&G1.uy[hown - kBX - kUYo]);
@@ -638,37 +558,30 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 }
             }
             Pair<T> hn;
-            hn.a = MODE == kModeU ? hpin.a : hpin.a - B.dtc2 * (dv0 - rp0);
-            hn.b = MODE == kModeU ? hpin.b : hpin.b - B.dtc2 * (dv1 - rp1);
+            hn.a = (hc.a & 1u) ? (MODE == kModeU ? hp.a : hp.a - B.dtc2 * (dv0 - rp0)) : T(0);
+            hn.b = (hc.b & 1u) ? (MODE == kModeU ? hp.b : hp.b - B.dtc2 * (dv1 - rp1)) : T(0);
             *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][hown - 2 * kBX]) = hn;
         } else if (hcol) {
-            S.pn[(t - 1) & 1][hown - 2 * kBX] = press1(G1, G2, hown, t - 1, hg, hpin.a);
+            S.pn[(t - 1) & 1][hown - 2 * kBX] = press1(G1, G2, hown, t - 1, hg);
         }
         pn_m = pn_new;
         s2 = s1;
         s1 = s0;
         s0 = s0 == kStages - 1 ? 0 : s0 + 1;
-        return true;
         };
     for (int t = t0; t <= tend; t += 5) {
-        if (!step(std::integral_constant<int, 0>{}, t)) { failed = true; break; }
+        step(std::integral_constant<int, 0>{}, t);
         if (t + 1 > tend) break;
-        if (!step(std::integral_constant<int, 1>{}, t + 1)) { failed = true; break; }
+        step(std::integral_constant<int, 1>{}, t + 1);
         if (t + 2 > tend) break;
-        if (!step(std::integral_constant<int, 2>{}, t + 2)) { failed = true; break; }
+        step(std::integral_constant<int, 2>{}, t + 2);
         if (t + 3 > tend) break;
-        if (!step(std::integral_constant<int, 3>{}, t + 3)) { failed = true; break; }
+        step(std::integral_constant<int, 3>{}, t + 3);
         if (t + 4 > tend) break;
-        if (!step(std::integral_constant<int, 4>{}, t + 4)) { failed = true; break; }
+        step(std::integral_constant<int, 4>{}, t + 4);
     }
-    if (failed) {
-        // a plane's copies did not complete in time: report, wait (bounded) for the copies
-        // still in flight so that none lands after the CTA has left, and stop
-        if (tid == 0 && B.err) atomicExch(B.err, 1);
-        for (int s = 0; s < kStages; ++s)
-            if ((pending >> s) & 1u) (void)mbar_wait(full_base + 8u * s, (phase >> s) & 1u);
-        return;
-    }
+    // drain this column's copies before the ring is reused
+    cp_async_wait<0>();
     if (REDUCE) {
         for (int q = 0; q < 4; ++q)
             for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
