@@ -63,7 +63,8 @@ typedef enum pm_status {
     PM_ERR_DIVERGED = 5,        /* NaN or Inf in the reductions */
     PM_ERR_OOM = 6,             /* device allocation failed */
     PM_ERR_CUDA = 7,            /* any other CUDA runtime error */
-    PM_ERR_TIMEOUT = 8,         /* a bounded device wait ran out */
+    PM_ERR_TIMEOUT = 8,         /* a bounded device wait ran out (reserved: no kernel of
+                                   this version waits on another thread or device) */
     PM_ERR_UNSUPPORTED = 9,     /* option combination not implemented */
     PM_ERR_TOO_LARGE = 10       /* domain exceeds pm_iterate_noalloc's fixed scratch */
 } pm_status;
@@ -124,7 +125,12 @@ typedef struct pm_options {
                                  choice when autotune is set, else persistent CTAs),
                                  -1 = persistent CTAs, n > 0 = one CTA per tile column
                                  and chunk of n planes */
-    int32_t reserved[6];
+    int32_t tile;             /* tiled kernel's tile shape: 0 = automatic (the autotuner's
+                                 choice when autotune is set, else 1); 1 = 64 x 12 cells,
+                                 two per thread; 2 = 64 x 12, four per thread; 3 = 64 x 8,
+                                 four per thread (FP32 fields; FP64 fields always use 1).
+                                 Every shape gives the same fields, bit for bit. */
+    int32_t reserved[5];
 } pm_options;
 
 typedef struct pm_stats {
@@ -150,6 +156,9 @@ typedef struct pm_stats {
     int64_t sweeps_timed_src; /* sweeps inside those timed windows */
     int64_t kernel_launches;  /* kernels launched by the call (a replayed window graph counts
                                  the kernels it holds) */
+    int32_t tile;             /* tiled kernel's tile shape used (pm_options.tile numbering;
+                                 0 = simple kernel) */
+    int32_t reserved;
 } pm_stats;
 
 /* Fills *opt with the defaults: tol 1e-6, check_every 200, max_iter 2e6,

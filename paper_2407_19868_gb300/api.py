@@ -60,7 +60,8 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("dt_safety", C.c_double), ("Re", C.c_double),
                 ("c2", C.c_double), ("use_graph", C.c_int32), ("check_percolation", C.c_int32),
                 ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
-                ("autotune", C.c_int32), ("schedule", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("autotune", C.c_int32), ("schedule", C.c_int32), ("tile", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class Stats(C.Structure):
@@ -69,7 +70,8 @@ class Stats(C.Structure):
                 ("sweep_ms", C.c_double), ("sweeps_timed", C.c_int64), ("dc_rounds", C.c_int32),
                 ("status", C.c_int32), ("percolates", C.c_int32), ("schedule", C.c_int32),
                 ("setup_seconds", C.c_double), ("n_fluid", C.c_int64), ("sweep_ms_src", C.c_double),
-                ("sweeps_timed_src", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("sweeps_timed_src", C.c_int64), ("kernel_launches", C.c_int64), ("tile", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {"iters": int(self.iters), "q": [float(v) for v in self.q], "delta": float(self.delta),
@@ -79,7 +81,8 @@ class Stats(C.Structure):
                 "status": int(self.status), "percolates": bool(self.percolates),
                 "schedule": int(self.schedule), "setup_seconds": float(self.setup_seconds),
                 "n_fluid": int(self.n_fluid), "sweep_ms_src": float(self.sweep_ms_src),
-                "sweeps_timed_src": int(self.sweeps_timed_src), "kernel_launches": int(self.kernel_launches)}
+                "sweeps_timed_src": int(self.sweeps_timed_src), "kernel_launches": int(self.kernel_launches),
+                "tile": int(self.tile)}
 
 
 _LIB = None

@@ -83,7 +83,6 @@ struct SweepBatch {
     int multi;             // 1: problems have their own geometry (tiled kernel, one unit per CTA)
     const int *active;     // device, per problem, 0 = skip (converged); nullptr = all active
     int pres_axis;         // fixed-pressure axis + 1 (reservoir layers 0 and n - 1); 0 = none
-    int *err;              // device flag set to 1 when a bounded wait of the tiled kernel ran out
     SweepProblem<T> prob[kMaxBatch];
 };
 

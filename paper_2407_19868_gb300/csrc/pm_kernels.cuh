@@ -68,6 +68,62 @@ __global__ void sanitize_kernel(const uint8_t *__restrict__ flags, long long N, 
     }
 }
 
+// ------------------------------------------------------------------ stencil codes
+// Layout: code_shift in pm_common.cuh.
+
+__device__ __forceinline__ bool cell_pore(const uint8_t *mask, int x, int y, int z, int nx, int ny, int nz,
+                                          const int per[3]) {
+    x = nb_coord(x, nx, per[0]);
+    y = nb_coord(y, ny, per[1]);
+    z = nb_coord(z, nz, per[2]);
+    if (x < 0 || y < 0 || z < 0) return false;
+    return mask[(long long)x + (long long)nx * ((long long)y + (long long)ny * z)] == 0;
+}
+
+__device__ __forceinline__ bool node_fluid_at(const uint8_t *mask, int d, int x, int y, int z, int nx, int ny,
+                                              int nz, const int per[3]) {
+    // coordinates may be up to 3 cells outside; wrap / wall handled per axis
+    if (!cell_pore(mask, x, y, z, nx, ny, nz, per)) return false;
+    return cell_pore(mask, x + (d == 0), y + (d == 1), z + (d == 2), nx, ny, nz, per);
+}
+
+__global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, int nz, int px, int py, int pz,
+                            uint32_t *__restrict__ code) {
+    const int per[3] = {px, py, pz};
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx);
+        const long long r = c / nx;
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        uint32_t w = 0;
+        if (mask[c] == 0) {
+            w |= 1u;
+            for (int d = 0; d < 3; ++d) {
+                if (!node_fluid_at(mask, d, x, y, z, nx, ny, nz, per)) continue;
+                w |= (uint32_t)node_bit(d);
+                for (int i = 0; i < 3; ++i) {
+                    if (i == d) continue;
+                    bool F[5];
+                    for (int m = -2; m <= 2; ++m) {
+                        if (m == 0) continue;
+                        F[m + 2] = node_fluid_at(mask, d, x + (i == 0) * m, y + (i == 1) * m, z + (i == 2) * m,
+                                                 nx, ny, nz, per);
+                    }
+                    // Fig. neighborhoodCases / Appendix B
+                    uint32_t k;
+                    if (!F[1] && !F[3]) k = 1u;                        // case 1
+                    else if (!F[1]) k = (F[4] ? 2u : 3u) | 4u;         // case 4 / 2
+                    else if (!F[3]) k = F[0] ? 2u : 3u;                // case 5 / 3
+                    else k = 0u;                                       // case 6
+                    w |= k << code_shift(d, i);
+                }
+            }
+        }
+        code[c] = w;
+    }
+}
+
 // ------------------------------------------------------------------ wall stencil
 // Sec. 4 / Appendix B: second derivative of a face velocity along an axis perpendicular
 // to its direction, from the node itself (u0) and the nodes at -2, -1, +1, +2 with their

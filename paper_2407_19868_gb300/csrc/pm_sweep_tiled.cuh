@@ -22,69 +22,9 @@
 
 namespace pmgb {
 
-// ------------------------------------------------------------------ stencil codes
-// (layout: see code_shift in pm_common.cuh)
-
-__device__ __forceinline__ bool cell_pore(const uint8_t *mask, int x, int y, int z, int nx, int ny, int nz,
-                                          const int per[3]) {
-    x = nb_coord(x, nx, per[0]);
-    y = nb_coord(y, ny, per[1]);
-    z = nb_coord(z, nz, per[2]);
-    if (x < 0 || y < 0 || z < 0) return false;
-    return mask[(long long)x + (long long)nx * ((long long)y + (long long)ny * z)] == 0;
-}
-
-__device__ __forceinline__ bool node_fluid_at(const uint8_t *mask, int d, int x, int y, int z, int nx, int ny,
-                                              int nz, const int per[3]) {
-    // coordinates may be up to 3 cells outside; wrap / wall handled per axis
-    if (!cell_pore(mask, x, y, z, nx, ny, nz, per)) return false;
-    return cell_pore(mask, x + (d == 0), y + (d == 1), z + (d == 2), nx, ny, nz, per);
-}
-
-__global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, int nz, int px, int py, int pz,
-                            uint32_t *__restrict__ code) {
-    const int per[3] = {px, py, pz};
-    const long long N = (long long)nx * ny * nz;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % nx);
-        const long long r = c / nx;
-        const int y = (int)(r % ny), z = (int)(r / ny);
-        uint32_t w = 0;
-        if (mask[c] == 0) {
-            w |= 1u;
-            for (int d = 0; d < 3; ++d) {
-                if (!node_fluid_at(mask, d, x, y, z, nx, ny, nz, per)) continue;
-                w |= (uint32_t)node_bit(d);
-                for (int i = 0; i < 3; ++i) {
-                    if (i == d) continue;
-                    bool F[5];
-                    for (int m = -2; m <= 2; ++m) {
-                        if (m == 0) continue;
-                        F[m + 2] = node_fluid_at(mask, d, x + (i == 0) * m, y + (i == 1) * m, z + (i == 2) * m,
-                                                 nx, ny, nz, per);
-                    }
-                    // Fig. neighborhoodCases / Appendix B
-                    uint32_t k;
-                    if (!F[1] && !F[3]) k = 1u;                        // case 1
-                    else if (!F[1]) k = (F[4] ? 2u : 3u) | 4u;         // case 4 / 2
-                    else if (!F[3]) k = F[0] ? 2u : 3u;                // case 5 / 3
-                    else k = 0u;                                       // case 6
-                    w |= k << code_shift(d, i);
-                }
-            }
-        }
-        code[c] = w;
-    }
-}
-
 // ------------------------------------------------------------------ cp.async helpers
 // 16-byte asynchronous global -> shared copies (L2 only: the tile is staged in shared
 // memory, nothing is reused from L1).
-__device__ __forceinline__ void cp_async16(void *s, const void *g) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
-}
 // zero-filling form: src_bytes = 0 reads nothing and writes 16 zero bytes
 __device__ __forceinline__ void cp_async16z(void *s, const void *g, unsigned src_bytes) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
@@ -96,34 +36,55 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// ------------------------------------------------------------------ kernel
-// Tile TX x TY cells, thread (lane, ty) owns the pair of cells (x0 + 2 lane, y0 + ty) and
-// (x0 + 2 lane + 1, y0 + ty).  Shared-memory boxes are BX = TX + 8 wide (x0 - 4 ..
-// x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4 high (y0 - 2 .. y0 + TY + 1); the
-// stencil needs +-2 in x and y.
-constexpr int kTX = 64, kTY = 12, kBX = kTX + 8, kBY = kTY + 4, kPL = kBX * kBY;
-// Ring of kStages planes: planes t-2, t-1, t are read in step t while the copies of the
-// next kAhead planes are in flight.
-constexpr int kStages = 5, kAhead = kStages - 3;
-// p^n, the input pressure and the stencil codes are needed on box rows 2 .. kTY + 2 (tile
-// rows and the +y halo row) only, u_y on rows 1 .. kTY + 2; u_x and u_z on all rows
-constexpr int kPNL = (kTY + 1) * kBX, kPNo = 2 * kBX;
-constexpr int kUYL = (kTY + 2) * kBX, kUYo = kBX;
-// CTAs per SM the FP32 kernel is built for (registers and shared memory)
-constexpr int kMinBlocks = 2;
-constexpr int kNT = (kTX / 2) * kTY;
+// ------------------------------------------------------------------ tile shapes
+// A CTA covers TX x TY cells of the (x, y) plane; each thread owns CPT x-adjacent cells
+// of one tile row (LPR = TX / CPT threads per row); the ring holds STAGES planes, AHEAD =
+// STAGES - 3 of them in flight; MINB CTAs per SM for FP32 (one for FP64).  Shared-memory
+// boxes are BX = TX + 8 wide (x0 - 4 .. x0 + TX + 3, whole 16-byte chunks) and BY = TY + 4
+// high (y0 - 2 .. y0 + TY + 1): the stencil reaches +-2 in x and y.  p^n, the input
+// pressure and the stencil codes are needed on box rows 2 .. TY + 2 only (tile rows and
+// the +y halo row), u_y on rows 1 .. TY + 2, u_x and u_z on all rows.
+template <int TX_, int TY_, int CPT_, int STAGES_, int MINB_>
+struct TileCfg {
+    static constexpr int TX = TX_, TY = TY_, CPT = CPT_, STAGES = STAGES_, MINB = MINB_;
+    static constexpr int LPR = TX / CPT, NT = LPR * TY, NW = NT / 32;
+    static constexpr int BX = TX + 8, BY = TY + 4, PL = BX * BY;
+    static constexpr int AHEAD = STAGES - 3;
+    static constexpr int PNL = (TY + 1) * BX, PNo = 2 * BX;
+    static constexpr int UYL = (TY + 2) * BX, UYo = BX;
+    static_assert(TX % CPT == 0 && 32 % LPR == 0 && NT % 32 == 0 && NW >= 2 && TY <= 32, "tile shape");
+    static_assert(CPT == 2 || CPT == 4, "cells per thread");
+    static_assert(AHEAD >= 1, "ring depth");
+};
+// The shapes the autotuner chooses from (pm_options.tile = index + 1).
+using Tile64x12c2 = TileCfg<64, 12, 2, 5, 2>;  // 384 threads, 2 CTAs / SM
+using Tile64x12c4 = TileCfg<64, 12, 4, 5, 2>;  // 192 threads, 2 CTAs / SM
+using Tile64x8c4 = TileCfg<64, 8, 4, 4, 3>;    // 128 threads, 3 CTAs / SM
+constexpr int kNumTiles = 3;
+// FP64 fields use the first shape only.
+template <typename T>
+inline int tile_count() {
+    return sizeof(T) == 4 ? kNumTiles : 1;
+}
+struct TileDims {
+    int tx, ty;
+};
+__host__ __device__ constexpr TileDims tile_dims(int t) {
+    return t == 2 ? TileDims{64, 8} : TileDims{64, 12};
+}
+constexpr int kMaxTileTX = 64;
 
 // One ring stage: the five arrays of one plane, contiguous, so that every access is a
 // per-step stage pointer plus a compile-time offset.  Arrays that need fewer box rows
-// start at a later row: u_y at row 1 (index = box index - kUYo), p and the codes at
-// row 2 (index = box index - kPNo).
-template <typename T>
+// start at a later row: u_y at row 1 (index = box index - UYo), p and the codes at row 2
+// (index = box index - PNo).
+template <typename T, class C>
 struct TiledStage {
-    T ux[kPL];
-    T uz[kPL];
-    T uy[kUYL];
-    T pin[kPNL];
-    uint32_t cd[kPNL];
+    T ux[C::PL];
+    T uz[C::PL];
+    T uy[C::UYL];
+    T pin[C::PNL];
+    uint32_t cd[C::PNL];
 };
 
 // Wall coefficients per wall kind.  Non-fluid nodes hold 0, so with S = u(-1) + u(+1)
@@ -138,14 +99,40 @@ struct alignas(2 * sizeof(T)) WallCoef {
     T A, K;
 };
 
-template <typename T>
+template <typename T, class C>
 struct TiledSmem {
-    TiledStage<T> st[kStages];
-    T pn[2][kPNL];  // index: box index - 2 kBX
+    TiledStage<T, C> st[C::STAGES];
+    T pn[2][C::PNL];  // index: box index - 2 BX
     WallCoef<T> coef[4];
 };
 
-// A pair of x-adjacent values (aligned for one 2-wide shared-memory access).
+// A group of N x-adjacent values, aligned for one vector access of up to 16 bytes.
+template <typename T, int N>
+struct alignas(N * sizeof(T) < 16 ? N * sizeof(T) : 16) VecT {
+    T v[N];
+};
+// Loads / stores of N x-adjacent values (shared or global), in 16-byte pieces at most.
+template <int N, typename T>
+__device__ __forceinline__ void ldv(T (&o)[N], const T *p) {
+    constexpr int E = (N * sizeof(T) <= 16) ? N : 16 / (int)sizeof(T);
+#pragma unroll
+    for (int i = 0; i < N; i += E) {
+        const VecT<T, E> w = *reinterpret_cast<const VecT<T, E> *>(p + i);
+#pragma unroll
+        for (int j = 0; j < E; ++j) o[i + j] = w.v[j];
+    }
+}
+template <int N, typename T>
+__device__ __forceinline__ void stv(T *p, const T (&a)[N]) {
+    constexpr int E = (N * sizeof(T) <= 16) ? N : 16 / (int)sizeof(T);
+#pragma unroll
+    for (int i = 0; i < N; i += E) {
+        VecT<T, E> w;
+#pragma unroll
+        for (int j = 0; j < E; ++j) w.v[j] = a[i + j];
+        *reinterpret_cast<VecT<T, E> *>(p + i) = w;
+    }
+}
 template <typename T>
 struct alignas(2 * sizeof(T)) Pair {
     T a, b;
@@ -153,10 +140,6 @@ struct alignas(2 * sizeof(T)) Pair {
 template <typename T>
 __device__ __forceinline__ Pair<T> ld2(const T *p) {
     return *reinterpret_cast<const Pair<T> *>(p);
-}
-template <typename T>
-__device__ __forceinline__ Pair<uint32_t> ld2u(const uint32_t *p) {
-    return *reinterpret_cast<const Pair<uint32_t> *>(p);
 }
 
 // Byte offset of the coefficient-table entry of the wall kind at bit sh of word c (one
@@ -168,20 +151,30 @@ __device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
     return (c >> (sh - lg)) & (3u << lg);
 }
 
-template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
-__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
+// ------------------------------------------------------------------ kernel
+// Thread (cx, ty) owns the cells x0 + CPT cx .. x0 + CPT cx + CPT - 1 of tile row y0 + ty.
+// Per step t the CTA
+//   reads plane t of its own cells into the z queues,
+//   forms p^n on plane t-1 (own cells and the +x / +y halo cells),
+//   updates u on plane t-2 with p^n of planes t-2 and t-1 and writes u^{n+1}, p^n.
+// Every shape does the same arithmetic per cell in the same order (bit-identical fields).
+template <typename T, class C, int MODE, bool REDUCE, bool SRC, bool ALPHA>
+__global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int tiles_x, int tiles_y,
                        long long per_cta, int zchunk) {
+    constexpr int TX = C::TX, TY = C::TY, CPT = C::CPT, BX = C::BX, BY = C::BY, NT = C::NT;
+    constexpr int STAGES = C::STAGES, AHEAD = C::AHEAD, PNo = C::PNo, UYo = C::UYo, PL = C::PL;
     // single geometry: B.nx.. and the arguments; multi-geometry: per problem (below)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TiledSmem<T> &S = *reinterpret_cast<TiledSmem<T> *>(smem_raw);
+    TiledSmem<T, C> &S = *reinterpret_cast<TiledSmem<T, C> *>(smem_raw);
     int nx = B.nx, ny = B.ny, nz = B.nz;
     long long N = B.N, plane = (long long)nx * ny;
     const int tid = threadIdx.x;
-    const int lane = tid & 31, ty = tid >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int cx = tid % C::LPR, ty = tid / C::LPR;
     const unsigned char *coef_bytes = reinterpret_cast<const unsigned char *>(S.coef);
     __shared__ double red_sum[kMaxSame][4];  // per drive: FP64 sums of this CTA
-    __shared__ double red[kNT / 32][4];
+    __shared__ double red[C::NW][4];
     if (REDUCE && tid < kMaxSame * 4) red_sum[tid / 4][tid % 4] = 0.0;
     // multi-geometry launch: this CTA's problem (prefix table of CTA counts)
     int mp = 0;
@@ -214,8 +207,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     // (short pieces, neighbouring columns again at similar planes).  Every CTA gets the
     // same number of plane steps, with at most one restart of its plane pipeline.
     // zchunk > 0 instead: one (column, plane chunk) unit per CTA, chunk-major order.
-    const long long G = gridDim.x, C = (long long)B.nprob * tiles_x * tiles_y;
-    const long long rounds = zchunk > 0 ? 0 : C / G, rem_total = zchunk > 0 ? 0 : (C - rounds * G) * nz;
+    const long long G = gridDim.x, Cn = (long long)B.nprob * tiles_x * tiles_y;
+    const long long rounds = zchunk > 0 ? 0 : Cn / G, rem_total = zchunk > 0 ? 0 : (Cn - rounds * G) * nz;
     long long pos = (long long)blockIdx.x * per_cta;
     const long long pos_end = min(rem_total, pos + per_cta);
     for (long long it = 0;; ++it) {
@@ -232,8 +225,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         m1 = min(nz, m0 + zc);
     } else if (zchunk > 0) {
         if (it > 0) break;
-        col = blockIdx.x % C;
-        m0 = (int)(blockIdx.x / C) * zchunk;
+        col = blockIdx.x % Cn;
+        m0 = (int)(blockIdx.x / Cn) * zchunk;
         m1 = min(nz, m0 + zchunk);
     } else if (it < rounds) {
         col = it * G + blockIdx.x;
@@ -249,49 +242,57 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     const int pi = (int)(col % B.nprob);
     const int tile = (int)(col / B.nprob);
     const int rs = B.multi ? 0 : pi;  // slot of red_sum
-    const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
     const SweepProblem<T> &P = B.prob[pi];
     const T *__restrict__ gux = P.uin;
     const T *__restrict__ guy = P.uin + N;
     const T *__restrict__ guz = P.uin + 2 * N;
     const T *__restrict__ gp = P.pin;
 
-    // Copy plan.  Field boxes are kBY rows of FCH 16-byte chunks, the code box kBY rows
+    // Copy plan.  Field boxes are BY rows of FCH 16-byte chunks, the code box TY + 1 rows
     // of CCH chunks; chunk starts are multiples of 4 cells (nx % 4 == 0), so a chunk
     // wraps around a periodic boundary as a whole.  fo / co: in-plane element offset of
     // this thread's field / code chunk (-1: none or outside a wall), fs / cs: its place
     // in the box.
-    constexpr int FE = 16 / (int)sizeof(T), FCH = kBX / FE, CCH = kBX / 4;
-    constexpr int FR = (FCH * kBY + kNT - 1) / kNT;
+    constexpr int FE = 16 / (int)sizeof(T), FCH = BX / FE, CCH = BX / 4;
+    constexpr int FR = (FCH * BY + NT - 1) / NT;
+    constexpr int CR = (CCH * (TY + 1) + NT - 1) / NT;
     int fo[FR], fs[FR];
     bool fhas[FR], fuy[FR], fp[FR];  // chunk exists / row also holds u_y / also p
 #pragma unroll
     for (int r = 0; r < FR; ++r) {
-        const int c = tid + r * kNT;
+        const int c = tid + r * NT;
         fo[r] = -1;
         fs[r] = 0;
-        fhas[r] = c < FCH * kBY;
+        fhas[r] = c < FCH * BY;
         fuy[r] = fp[r] = false;
         if (fhas[r]) {
             const int hy = c / FCH, hx = (c % FCH) * FE;
-            fs[r] = hy * kBX + hx;
-            fuy[r] = hy >= 1 && hy <= kTY + 2;
-            fp[r] = hy >= 2 && hy <= kTY + 2;
+            fs[r] = hy * BX + hx;
+            fuy[r] = hy >= 1 && hy <= TY + 2;
+            fp[r] = hy >= 2 && hy <= TY + 2;
             const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
             if (gx >= 0 && gy >= 0) fo[r] = gx + nx * gy;
         }
     }
-    // code chunks: box rows 2 .. kTY + 2; cs is the index in the stage's code array
-    int co = -1, cs = 0;
-    const bool chas = tid < CCH * (kTY + 1);
-    if (chas) {
-        const int hy = 2 + tid / CCH, hx = (tid % CCH) * 4;
-        cs = hy * kBX + hx - kPNo;
-        const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
-        if (gx >= 0 && gy >= 0) co = gx + nx * gy;
+    // code chunks: box rows 2 .. TY + 2; cs is the index in the stage's code array
+    int co[CR], cs[CR];
+    bool chas[CR];
+#pragma unroll
+    for (int r = 0; r < CR; ++r) {
+        const int c = tid + r * NT;
+        co[r] = -1;
+        cs[r] = 0;
+        chas[r] = c < CCH * (TY + 1);
+        if (chas[r]) {
+            const int hy = 2 + c / CCH, hx = (c % CCH) * 4;
+            cs[r] = hy * BX + hx - PNo;
+            const int gx = nb_coord(x0 - 4 + hx, nx, B.per[0]), gy = nb_coord(y0 - 2 + hy, ny, B.per[1]);
+            if (gx >= 0 && gy >= 0) co[r] = gx + nx * gy;
+        }
     }
     auto issue_plane = [&](int k, int slot) {
-        TiledStage<T> &G = S.st[slot];
+        TiledStage<T, C> &Gs = S.st[slot];
         const int gz = nb_coord(k, nz, B.per[2]);
         const long long po = (long long)gz * plane;
 #pragma unroll
@@ -302,21 +303,23 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             const bool in = gz >= 0 && fo[r] >= 0;
             const long long o = in ? po + fo[r] : 0;
             const unsigned nb = in ? 16u : 0u;
-            cp_async16z(&G.ux[e], gux + o, nb);
-            cp_async16z(&G.uz[e], guz + o, nb);
-            if (fuy[r]) cp_async16z(&G.uy[e - kUYo], guy + o, nb);
-            if (fp[r]) cp_async16z(&G.pin[e - kPNo], gp + o, nb);
+            cp_async16z(&Gs.ux[e], gux + o, nb);
+            cp_async16z(&Gs.uz[e], guz + o, nb);
+            if (fuy[r]) cp_async16z(&Gs.uy[e - UYo], guy + o, nb);
+            if (fp[r]) cp_async16z(&Gs.pin[e - PNo], gp + o, nb);
         }
-        if (chas) {
-            const bool in = gz >= 0 && co >= 0;
-            cp_async16z(&G.cd[cs], code + (in ? po + co : 0), in ? 16u : 0u);
+#pragma unroll
+        for (int r = 0; r < CR; ++r) {
+            if (!chas[r]) continue;
+            const bool in = gz >= 0 && co[r] >= 0;
+            cp_async16z(&Gs.cd[cs[r]], code + (in ? po + co[r] : 0), in ? 16u : 0u);
         }
         cp_async_commit();
     };
 
-    const int own = (ty + 2) * kBX + 4 + 2 * lane;  // box index of the first cell of the pair
-    const int gx_own = x0 + 2 * lane, gy_own = y0 + ty;
-    const bool real0 = gx_own < nx && gy_own < ny;       // nx % 4 == 0: both cells or neither
+    const int own = (ty + 2) * BX + 4 + CPT * cx;  // box index of the first own cell
+    const int gx_own = x0 + CPT * cx, gy_own = y0 + ty;
+    const bool real0 = gx_own < nx && gy_own < ny;       // nx % 4 == 0: all own cells or none
     const long long gin_own = (long long)gx_own + (long long)nx * gy_own;
     // tile positions past the domain edge stand for their periodic image (or for solid
     // outside a wall): their pressure is formed at the wrapped index, nothing is written
@@ -325,52 +328,53 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         const int wx = nb_coord(gx_own, nx, B.per[0]), wy = nb_coord(gy_own, ny, B.per[1]);
         if (wx >= 0 && wy >= 0) gin_wrap = (long long)wx + (long long)nx * wy;
     }
-    // halo p^n: the last warp takes the row y0 + TY (pairs), the last TY lanes of the
-    // warp before it the column x0 + TX (single cells); for FP32 these lanes issue no
-    // copies (288 chunks per array), which balances the work before the barrier
-    const bool hrow = ty == kTY - 1, hcol = ty == kTY - 2 && lane >= 32 - kTY;
-    const int hown = hrow ? (kTY + 2) * kBX + 4 + 2 * lane : (lane - (32 - kTY) + 2) * kBX + kTX + 4;
+    // halo p^n: the threads of the last tile row take the row y0 + TY (CPT cells each), the
+    // last TY lanes of the warp before the last one the column x0 + TX (single cells)
+    const bool hrow = ty == TY - 1, hcol = warp == C::NW - 2 && lane >= 32 - TY;
+    const int hown = hrow ? (TY + 2) * BX + 4 + CPT * cx : (lane - (32 - TY) + 2) * BX + TX + 4;
     long long hg = -1;
     if ((hrow || hcol) && SRC) {
-        const int gx = nb_coord(x0 + (hown % kBX) - 4, nx, B.per[0]), gy = nb_coord(y0 + hown / kBX - 2, ny, B.per[1]);
+        const int gx = nb_coord(x0 + (hown % BX) - 4, nx, B.per[0]), gy = nb_coord(y0 + hown / BX - 2, ny, B.per[1]);
         if (gx >= 0 && gy >= 0) hg = (long long)gx + (long long)nx * gy;
     }
     // offsets to the +x / +y cell for the drag term; at a wall the face is not fluid and the
     // value is discarded, so the cell itself stands in (keeps the read in bounds)
-    const int wxp = nb_coord(gx_own + 2, nx, B.per[0]), wyp = nb_coord(gy_own + 1, ny, B.per[1]);
-    const long long ex1_off = wxp >= 0 ? (long long)wxp - (gx_own + 1) : 0;  // second cell's +x
+    const int wxp = nb_coord(gx_own + CPT, nx, B.per[0]), wyp = nb_coord(gy_own + 1, ny, B.per[1]);
+    const long long exl_off = wxp >= 0 ? (long long)wxp - (gx_own + CPT) : -1;  // last cell's +x
     const long long ey_off = wyp >= 0 ? ((long long)wyp - gy_own) * nx : 0;
 
-    Pair<T> qx[5], qy[5], qz[5];
+    T qx[5][CPT], qy[5][CPT], qz[5][CPT];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) qx[i] = qy[i] = Pair<T>{T(0), T(0)};
+    for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int i = 0; i < 5; ++i) qz[i] = Pair<T>{T(0), T(0)};
-    Pair<T> pn_m{T(0), T(0)};  // own p^n on the plane being updated (m)
+        for (int j = 0; j < CPT; ++j) qx[i][j] = qy[i][j] = qz[i][j] = T(0);
+    T pn_m[CPT];  // own p^n on the plane being updated (m)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) pn_m[j] = T(0);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 
     const int t0 = m0 - 2;
-    int s2 = ((t0 - 2) % kStages + kStages) % kStages;  // ring stages of planes t-2, t-1, t
-    int s1 = (s2 + 1) % kStages, s0 = (s2 + 2) % kStages;
+    int s2 = ((t0 - 2) % STAGES + STAGES) % STAGES;  // ring stages of planes t-2, t-1, t
+    int s1 = (s2 + 1) % STAGES, s0 = (s2 + 2) % STAGES;
     {
         int sl = s0;
-        for (int k = 0; k < kAhead; ++k) {
+        for (int k = 0; k < AHEAD; ++k) {
             issue_plane(t0 + k, sl);
-            sl = sl == kStages - 1 ? 0 : sl + 1;
+            sl = sl == STAGES - 1 ? 0 : sl + 1;
         }
     }
 
     // p^n of one cell at box position e of plane k (stage K), the plane below in KM
-    auto press1 = [&](const TiledStage<T> &K, const TiledStage<T> &KM, int e, int k, long long g) -> T {
-        const T dv = (K.ux[e] - K.ux[e - 1]) + (K.uy[e - kUYo] - K.uy[e - kBX - kUYo]) + (K.uz[e] - KM.uz[e]);
+    auto press1 = [&](const TiledStage<T, C> &K, const TiledStage<T, C> &KM, int e, int k, long long g) -> T {
+        const T dv = (K.ux[e] - K.ux[e - 1]) + (K.uy[e - UYo] - K.uy[e - BX - UYo]) + (K.uz[e] - KM.uz[e]);
         T rp = T(0);
         if (SRC && g >= 0) {
             const int gz = nb_coord(k, nz, B.per[2]);
             if (gz >= 0) rp = P.src[3 * N + (long long)gz * plane + g];
         }
-        const T p0 = K.pin[e - kPNo];
+        const T p0 = K.pin[e - PNo];
         const T pn = MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
-        return (K.cd[e - kPNo] & 1u) ? pn : T(0);
+        return (K.cd[e - PNo] & 1u) ? pn : T(0);
     };
     // second derivative across the flow (Appendix B) from the 3-bit wall code, added to lap
     auto perp = [&](T &lap, uint32_t cc, int sh, T um2, T um1, T u0, T up1, T up2) {
@@ -390,184 +394,207 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     // entries 0 .. 2) lives in slot (kRot + 1 + k) % 5.  The loop below unrolls five steps.
     auto step = [&](auto Rc, int t) {
         constexpr int kRot = decltype(Rc)::value;
-        cp_async_wait<kAhead - 1>();
+        constexpr int Q0 = (kRot + 1) % 5, Q1 = (kRot + 2) % 5, Q2 = (kRot + 3) % 5, Q3 = (kRot + 4) % 5,
+                      Q4 = kRot % 5;
+        cp_async_wait<AHEAD - 1>();
         __syncthreads();
         {
-            int sl = s0 + kAhead;
-            if (sl >= kStages) sl -= kStages;
-            issue_plane(t + kAhead, sl);
+            int sl = s0 + AHEAD;
+            if (sl >= STAGES) sl -= STAGES;
+            issue_plane(t + AHEAD, sl);
         }
-        const TiledStage<T> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
-        // z queues of the own column pair
-        qx[kRot % 5] = ld2(&G0.ux[own]);
-        qy[kRot % 5] = ld2(&G0.uy[own - kUYo]);
-        qz[(kRot + 3) % 5] = ld2(&G1.uz[own]);
+        const TiledStage<T, C> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
+        // z queues of the own cells
+        ldv(qx[Q4], &G0.ux[own]);
+        ldv(qy[Q4], &G0.uy[own - UYo]);
+        ldv(qz[(kRot + 3) % 5], &G1.uz[own]);
         // own p^n on plane t-1 (kept in registers until after the update of plane t-2)
-        Pair<T> pn_new;
+        T pn_new[CPT];
         {
-            const Pair<uint32_t> cd = ld2u<T>(&G1.cd[own - kPNo]);
-            const Pair<T> pin = ld2(&G1.pin[own - kPNo]);
-            const Pair<T> uyd = ld2(&G1.uy[own - kBX - kUYo]);
+            uint32_t cd[CPT];
+            T pin[CPT], uyd[CPT];
+            ldv(cd, &G1.cd[own - PNo]);
+            ldv(pin, &G1.pin[own - PNo]);
+            ldv(uyd, &G1.uy[own - BX - UYo]);
             const T uxl = G1.ux[own - 1];
-            T dv0 = (qx[(kRot + 1 + 3) % 5].a - uxl) + (qy[(kRot + 1 + 3) % 5].a - uyd.a) + (qz[(kRot + 1 + 2) % 5].a - qz[(kRot + 1 + 1) % 5].a);
-            T dv1 = (qx[(kRot + 1 + 3) % 5].b - qx[(kRot + 1 + 3) % 5].a) + (qy[(kRot + 1 + 3) % 5].b - uyd.b) + (qz[(kRot + 1 + 2) % 5].b - qz[(kRot + 1 + 1) % 5].b);
-            T rp0 = T(0), rp1 = T(0);
+            T rp[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) rp[j] = T(0);
             if (SRC && gin_wrap >= 0) {
                 const int gz = nb_coord(t - 1, nz, B.per[2]);
-                if (gz >= 0) {
-                    const Pair<T> r = ld2(P.src + 3 * N + (long long)gz * plane + gin_wrap);
-                    rp0 = r.a;
-                    rp1 = r.b;
-                }
+                if (gz >= 0) ldv(rp, P.src + 3 * N + (long long)gz * plane + gin_wrap);
             }
-            const bool pore0 = cd.a & 1u, pore1 = cd.b & 1u;
-            pn_new.a = pore0 ? (MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0)) : T(0);
-            pn_new.b = pore1 ? (MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1)) : T(0);
-            if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) {
-                dv0 = pore0 ? dv0 : T(0);
-                dv1 = pore1 ? dv1 : T(0);
-                acc[3] += (double)dv0 * (double)dv0 + (double)dv1 * (double)dv1;
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const T left = j == 0 ? uxl : qx[Q3][j - 1];
+                T dv = (qx[Q3][j] - left) + (qy[Q3][j] - uyd[j]) + (qz[(kRot + 1 + 2) % 5][j] - qz[(kRot + 1 + 1) % 5][j]);
+                const bool pore = cd[j] & 1u;
+                pn_new[j] = pore ? (MODE == kModeU ? pin[j] : pin[j] - B.dtc2 * (dv - rp[j])) : T(0);
+                if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) {
+                    dv = pore ? dv : T(0);
+                    acc[3] += (double)dv * (double)dv;
+                }
             }
         }
         const int m = t - 2;
         if (m >= m0 && real0) {
             // ------------------------------------------------------ update on plane m
-            Pair<T> ux_n, uy_n, uz_n;
+            T ux_n[CPT], uy_n[CPT], uz_n[CPT];
             if (MODE == kModeP) {
-                ux_n = qx[(kRot + 1 + 2) % 5];
-                uy_n = qy[(kRot + 1 + 2) % 5];
-                uz_n = qz[(kRot + 1 + 1) % 5];
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    ux_n[j] = qx[Q2][j];
+                    uy_n[j] = qy[Q2][j];
+                    uz_n[j] = qz[(kRot + 1 + 1) % 5][j];
+                }
             } else {
-                const Pair<uint32_t> c = ld2u<T>(&G2.cd[own - kPNo]);
-                const T *PN = S.pn[m & 1];  // index: box index - 2 kBX
+                uint32_t c[CPT];
+                ldv(c, &G2.cd[own - PNo]);
+                const T *PN = S.pn[m & 1];  // index: box index - 2 BX
                 const T *ux = G2.ux, *uy = G2.uy, *uz = G2.uz;
                 const long long gidx = (long long)m * plane + gin_own;
                 // u_x: along x (box), across y (box) and z (queue)
                 {
-                    const Pair<T> u0 = qx[(kRot + 1 + 2) % 5];
-                    const Pair<T> L = ld2(&ux[own - 2]), R = ld2(&ux[own + 2]);
-                    const Pair<T> ym2 = ld2(&ux[own - 2 * kBX]), ym1 = ld2(&ux[own - kBX]);
-                    const Pair<T> yp1 = ld2(&ux[own + kBX]), yp2 = ld2(&ux[own + 2 * kBX]);
-                    T lap0 = fma(T(-2), u0.a, u0.b + L.b);
-                    T lap1 = fma(T(-2), u0.b, R.a + u0.a);
-                    perp(lap0, c.a, code_shift(0, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
-                    perp(lap1, c.b, code_shift(0, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
-                    perp(lap0, c.a, code_shift(0, 2), qx[(kRot + 1 + 0) % 5].a, qx[(kRot + 1 + 1) % 5].a, u0.a, qx[(kRot + 1 + 3) % 5].a, qx[(kRot + 1 + 4) % 5].a);
-                    perp(lap1, c.b, code_shift(0, 2), qx[(kRot + 1 + 0) % 5].b, qx[(kRot + 1 + 1) % 5].b, u0.b, qx[(kRot + 1 + 3) % 5].b, qx[(kRot + 1 + 4) % 5].b);
-                    if (ALPHA) {
-                        lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + 1]) * u0.a;
-                        lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ex1_off]) * u0.b;
+                    const T *u0 = qx[Q2];
+                    const Pair<T> L = ld2(&ux[own - 2]), R = ld2(&ux[own + CPT]);
+                    T ym2[CPT], ym1[CPT], yp1[CPT], yp2[CPT], ext[CPT + 4], sx[CPT];
+                    ldv(ym2, &ux[own - 2 * BX]);
+                    ldv(ym1, &ux[own - BX]);
+                    ldv(yp1, &ux[own + BX]);
+                    ldv(yp2, &ux[own + 2 * BX]);
+                    ext[0] = L.a;
+                    ext[1] = L.b;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) ext[j + 2] = u0[j];
+                    ext[CPT + 2] = R.a;
+                    ext[CPT + 3] = R.b;
+                    if (SRC) ldv(sx, P.src + gidx);
+                    const T pr = PN[own - 2 * BX + CPT];
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        T lap = fma(T(-2), u0[j], ext[j + 3] + ext[j + 1]);
+                        perp(lap, c[j], code_shift(0, 1), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
+                        perp(lap, c[j], code_shift(0, 2), qx[Q0][j], qx[Q1][j], u0[j], qx[Q3][j], qx[Q4][j]);
+                        if (ALPHA) {
+                            const long long xr = gidx + j + 1 + (j == CPT - 1 ? exl_off : 0);
+                            lap -= T(0.5) * (B.alpha[gidx + j] + B.alpha[xr]) * u0[j];
+                        }
+                        const T right = j == CPT - 1 ? pr : pn_m[j + 1];
+                        T R0 = fma(B.inv_re, lap, P.f[0] - (right - pn_m[j]));
+                        if (SRC) R0 += sx[j];
+                        ux_n[j] = (c[j] & node_bit(0)) ? fma(B.dt, R0, u0[j]) : u0[j];
                     }
-                    const T pr = PN[own - 2 * kBX + 2];
-                    T R0 = fma(B.inv_re, lap0, P.f[0] - (pn_m.b - pn_m.a));
-                    T R1 = fma(B.inv_re, lap1, P.f[0] - (pr - pn_m.b));
-                    if (SRC) {
-                        const Pair<T> sx = ld2(P.src + gidx);
-                        R0 += sx.a;
-                        R1 += sx.b;
-                    }
-                    ux_n.a = (c.a & node_bit(0)) ? fma(B.dt, R0, u0.a) : u0.a;
-                    ux_n.b = (c.b & node_bit(0)) ? fma(B.dt, R1, u0.b) : u0.b;
                 }
                 // u_y: along y (box), across x (box) and z (queue)
                 {
-                    const Pair<T> u0 = qy[(kRot + 1 + 2) % 5];
-                    const int oy = own - kUYo;
-                    const Pair<T> L = ld2(&uy[oy - 2]), R = ld2(&uy[oy + 2]);
-                    const Pair<T> ym1 = ld2(&uy[oy - kBX]), yp1 = ld2(&uy[oy + kBX]);
-                    T lap0 = fma(T(-2), u0.a, yp1.a + ym1.a);
-                    T lap1 = fma(T(-2), u0.b, yp1.b + ym1.b);
-                    perp(lap0, c.a, code_shift(1, 0), L.a, L.b, u0.a, u0.b, R.a);
-                    perp(lap1, c.b, code_shift(1, 0), L.b, u0.a, u0.b, R.a, R.b);
-                    perp(lap0, c.a, code_shift(1, 2), qy[(kRot + 1 + 0) % 5].a, qy[(kRot + 1 + 1) % 5].a, u0.a, qy[(kRot + 1 + 3) % 5].a, qy[(kRot + 1 + 4) % 5].a);
-                    perp(lap1, c.b, code_shift(1, 2), qy[(kRot + 1 + 0) % 5].b, qy[(kRot + 1 + 1) % 5].b, u0.b, qy[(kRot + 1 + 3) % 5].b, qy[(kRot + 1 + 4) % 5].b);
-                    if (ALPHA) {
-                        lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[gidx + ey_off]) * u0.a;
-                        lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[gidx + 1 + ey_off]) * u0.b;
+                    const T *u0 = qy[Q2];
+                    const int oy = own - UYo;
+                    const Pair<T> L = ld2(&uy[oy - 2]), R = ld2(&uy[oy + CPT]);
+                    T ym1[CPT], yp1[CPT], pny[CPT], ext[CPT + 4], sy[CPT];
+                    ldv(ym1, &uy[oy - BX]);
+                    ldv(yp1, &uy[oy + BX]);
+                    ldv(pny, &PN[own - BX]);
+                    ext[0] = L.a;
+                    ext[1] = L.b;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) ext[j + 2] = u0[j];
+                    ext[CPT + 2] = R.a;
+                    ext[CPT + 3] = R.b;
+                    if (SRC) ldv(sy, P.src + N + gidx);
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        T lap = fma(T(-2), u0[j], yp1[j] + ym1[j]);
+                        perp(lap, c[j], code_shift(1, 0), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
+                        perp(lap, c[j], code_shift(1, 2), qy[Q0][j], qy[Q1][j], u0[j], qy[Q3][j], qy[Q4][j]);
+                        if (ALPHA) lap -= T(0.5) * (B.alpha[gidx + j] + B.alpha[gidx + j + ey_off]) * u0[j];
+                        T R0 = fma(B.inv_re, lap, P.f[1] - (pny[j] - pn_m[j]));
+                        if (SRC) R0 += sy[j];
+                        uy_n[j] = (c[j] & node_bit(1)) ? fma(B.dt, R0, u0[j]) : u0[j];
                     }
-                    const Pair<T> pny = ld2(&PN[own - kBX]);
-                    T R0 = fma(B.inv_re, lap0, P.f[1] - (pny.a - pn_m.a));
-                    T R1 = fma(B.inv_re, lap1, P.f[1] - (pny.b - pn_m.b));
-                    if (SRC) {
-                        const Pair<T> sy = ld2(P.src + N + gidx);
-                        R0 += sy.a;
-                        R1 += sy.b;
-                    }
-                    uy_n.a = (c.a & node_bit(1)) ? fma(B.dt, R0, u0.a) : u0.a;
-                    uy_n.b = (c.b & node_bit(1)) ? fma(B.dt, R1, u0.b) : u0.b;
                 }
                 // u_z: along z (queue), across x and y (box)
                 {
-                    const Pair<T> u0 = qz[(kRot + 1 + 1) % 5];
-                    const Pair<T> L = ld2(&uz[own - 2]), R = ld2(&uz[own + 2]);
-                    const Pair<T> ym2 = ld2(&uz[own - 2 * kBX]), ym1 = ld2(&uz[own - kBX]);
-                    const Pair<T> yp1 = ld2(&uz[own + kBX]), yp2 = ld2(&uz[own + 2 * kBX]);
-                    T lap0 = fma(T(-2), u0.a, qz[(kRot + 1 + 2) % 5].a + qz[(kRot + 1 + 0) % 5].a);
-                    T lap1 = fma(T(-2), u0.b, qz[(kRot + 1 + 2) % 5].b + qz[(kRot + 1 + 0) % 5].b);
-                    perp(lap0, c.a, code_shift(2, 0), L.a, L.b, u0.a, u0.b, R.a);
-                    perp(lap1, c.b, code_shift(2, 0), L.b, u0.a, u0.b, R.a, R.b);
-                    perp(lap0, c.a, code_shift(2, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
-                    perp(lap1, c.b, code_shift(2, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
+                    const T *u0 = qz[(kRot + 1 + 1) % 5];
+                    const Pair<T> L = ld2(&uz[own - 2]), R = ld2(&uz[own + CPT]);
+                    T ym2[CPT], ym1[CPT], yp1[CPT], yp2[CPT], ext[CPT + 4], sz[CPT];
+                    ldv(ym2, &uz[own - 2 * BX]);
+                    ldv(ym1, &uz[own - BX]);
+                    ldv(yp1, &uz[own + BX]);
+                    ldv(yp2, &uz[own + 2 * BX]);
+                    ext[0] = L.a;
+                    ext[1] = L.b;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) ext[j + 2] = u0[j];
+                    ext[CPT + 2] = R.a;
+                    ext[CPT + 3] = R.b;
+                    if (SRC) ldv(sz, P.src + 2 * N + gidx);
+                    long long g2 = 0;
                     if (ALPHA) {
                         const int zp = nb_coord(m + 1, nz, B.per[2]);
-                        const long long g2 = (long long)(zp >= 0 ? zp : m) * plane + gin_own;
-                        lap0 -= T(0.5) * (B.alpha[gidx] + B.alpha[g2]) * u0.a;
-                        lap1 -= T(0.5) * (B.alpha[gidx + 1] + B.alpha[g2 + 1]) * u0.b;
+                        g2 = (long long)(zp >= 0 ? zp : m) * plane + gin_own;
                     }
-                    T R0 = fma(B.inv_re, lap0, P.f[2] - (pn_new.a - pn_m.a));
-                    T R1 = fma(B.inv_re, lap1, P.f[2] - (pn_new.b - pn_m.b));
-                    if (SRC) {
-                        const Pair<T> sz = ld2(P.src + 2 * N + gidx);
-                        R0 += sz.a;
-                        R1 += sz.b;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        T lap = fma(T(-2), u0[j], qz[(kRot + 1 + 2) % 5][j] + qz[(kRot + 1 + 0) % 5][j]);
+                        perp(lap, c[j], code_shift(2, 0), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
+                        perp(lap, c[j], code_shift(2, 1), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
+                        if (ALPHA) lap -= T(0.5) * (B.alpha[gidx + j] + B.alpha[g2 + j]) * u0[j];
+                        T R0 = fma(B.inv_re, lap, P.f[2] - (pn_new[j] - pn_m[j]));
+                        if (SRC) R0 += sz[j];
+                        uz_n[j] = (c[j] & node_bit(2)) ? fma(B.dt, R0, u0[j]) : u0[j];
                     }
-                    uz_n.a = (c.a & node_bit(2)) ? fma(B.dt, R0, u0.a) : u0.a;
-                    uz_n.b = (c.b & node_bit(2)) ? fma(B.dt, R1, u0.b) : u0.b;
                 }
             }
-            *reinterpret_cast<Pair<T> *>(outx) = ux_n;
-            *reinterpret_cast<Pair<T> *>(outx + N) = uy_n;
-            *reinterpret_cast<Pair<T> *>(outx + 2 * N) = uz_n;
-            *reinterpret_cast<Pair<T> *>(outp) = pn_m;
+            stv(outx, ux_n);
+            stv(outx + N, uy_n);
+            stv(outx + 2 * N, uz_n);
+            stv(outp, pn_m);
             outx += plane;
             outp += plane;
             if (REDUCE) {
-                acc[0] += (double)ux_n.a + (double)ux_n.b;
-                acc[1] += (double)uy_n.a + (double)uy_n.b;
-                acc[2] += (double)uz_n.a + (double)uz_n.b;
-            }
-        }
-        // publish p^n of plane t-1 (own pair and halo cells) for the next step's update
-        *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own - 2 * kBX]) = pn_new;
-        if (hrow) {
-            // the +y halo row as pairs (same arithmetic as press1, 2-wide loads)
-            const Pair<uint32_t> hc = ld2u<T>(&G1.cd[hown - kPNo]);
-            const Pair<T> hp = ld2(&G1.pin[hown - kPNo]);
-            const Pair<T> hux = ld2(&G1.ux[hown]);
-            const T huxl = G1.ux[hown - 1];
-            const Pair<T> huy = ld2(&G1.uy[hown - kUYo]), huyd = ld2(&G1.uy[hown - kBX - kUYo]);
-            const Pair<T> huz = ld2(&G1.uz[hown]), huzd = ld2(&G2.uz[hown]);
-            const T dv0 = (hux.a - huxl) + (huy.a - huyd.a) + (huz.a - huzd.a);
-            const T dv1 = (hux.b - hux.a) + (huy.b - huyd.b) + (huz.b - huzd.b);
-            T rp0 = T(0), rp1 = T(0);
-            if (SRC && hg >= 0) {
-                const int gz = nb_coord(t - 1, nz, B.per[2]);
-                if (gz >= 0) {
-                    rp0 = P.src[3 * N + (long long)gz * plane + hg];
-                    rp1 = P.src[3 * N + (long long)gz * plane + hg + 1];
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    acc[0] += (double)ux_n[j];
+                    acc[1] += (double)uy_n[j];
+                    acc[2] += (double)uz_n[j];
                 }
             }
-            Pair<T> hn;
-            hn.a = (hc.a & 1u) ? (MODE == kModeU ? hp.a : hp.a - B.dtc2 * (dv0 - rp0)) : T(0);
-            hn.b = (hc.b & 1u) ? (MODE == kModeU ? hp.b : hp.b - B.dtc2 * (dv1 - rp1)) : T(0);
-            *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][hown - 2 * kBX]) = hn;
-        } else if (hcol) {
-            S.pn[(t - 1) & 1][hown - 2 * kBX] = press1(G1, G2, hown, t - 1, hg);
         }
-        pn_m = pn_new;
+        // publish p^n of plane t-1 (own cells and halo cells) for the next step's update
+        stv(&S.pn[(t - 1) & 1][own - 2 * BX], pn_new);
+        if (hrow) {
+            // the +y halo row, CPT cells per thread (same arithmetic as press1)
+            uint32_t hc[CPT];
+            T hp[CPT], hux[CPT], huy[CPT], huyd[CPT], huz[CPT], huzd[CPT], hr[CPT], hn[CPT];
+            ldv(hc, &G1.cd[hown - PNo]);
+            ldv(hp, &G1.pin[hown - PNo]);
+            ldv(hux, &G1.ux[hown]);
+            const T huxl = G1.ux[hown - 1];
+            ldv(huy, &G1.uy[hown - UYo]);
+            ldv(huyd, &G1.uy[hown - BX - UYo]);
+            ldv(huz, &G1.uz[hown]);
+            ldv(huzd, &G2.uz[hown]);
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) hr[j] = T(0);
+            if (SRC && hg >= 0) {
+                const int gz = nb_coord(t - 1, nz, B.per[2]);
+                if (gz >= 0) ldv(hr, P.src + 3 * N + (long long)gz * plane + hg);
+            }
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const T left = j == 0 ? huxl : hux[j - 1];
+                const T dv = (hux[j] - left) + (huy[j] - huyd[j]) + (huz[j] - huzd[j]);
+                hn[j] = (hc[j] & 1u) ? (MODE == kModeU ? hp[j] : hp[j] - B.dtc2 * (dv - hr[j])) : T(0);
+            }
+            stv(&S.pn[(t - 1) & 1][hown - 2 * BX], hn);
+        } else if (hcol) {
+            S.pn[(t - 1) & 1][hown - 2 * BX] = press1(G1, G2, hown, t - 1, hg);
+        }
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) pn_m[j] = pn_new[j];
         s2 = s1;
         s1 = s0;
-        s0 = s0 == kStages - 1 ? 0 : s0 + 1;
+        s0 = s0 == STAGES - 1 ? 0 : s0 + 1;
         };
     for (int t = t0; t <= tend; t += 5) {
         step(std::integral_constant<int, 0>{}, t);
@@ -586,16 +613,17 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         for (int q = 0; q < 4; ++q)
             for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
         if (lane == 0)
-            for (int q = 0; q < 4; ++q) red[ty][q] = acc[q];
+            for (int q = 0; q < 4; ++q) red[warp][q] = acc[q];
         __syncthreads();
         if (tid < 4) {
             double sum = 0.0;
-            for (int w = 0; w < kNT / 32; ++w) sum += red[w][tid];
+            for (int w = 0; w < C::NW; ++w) sum += red[w][tid];
             red_sum[rs][tid] += sum;
         }
     }
     __syncthreads();
     }  // persistent loop
+    (void)PL;
     if (REDUCE) {
         if (B.multi) {
             if (tid < 4) B.prob[mp].partials[((long long)blockIdx.x - B.prob[mp].unit_begin) * 4 + tid] = red_sum[0][tid];
@@ -639,20 +667,28 @@ inline int tiled_grid_size() {
     return sms;
 }
 
-// Launch geometry.  zchunk = 0: persistent CTAs (kMinBlocks per SM, whole-column rounds
-// then equal plane ranges); zchunk > 0: one CTA per (column, chunk of zchunk planes).
+// CTAs per SM of a tile shape (FP64: one).
 template <typename T>
-inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1, int zchunk = 0) {
+inline int tile_min_blocks(int tile) {
+    if (sizeof(T) != 4) return 1;
+    return tile == 0 ? Tile64x12c2::MINB : (tile == 1 ? Tile64x12c4::MINB : Tile64x8c4::MINB);
+}
+
+// Launch geometry.  zchunk = 0: persistent CTAs (MINB per SM, whole-column rounds then
+// equal plane ranges); zchunk > 0: one CTA per (column, chunk of zchunk planes).
+template <typename T>
+inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1, int zchunk = 0, int tile = 0) {
     TiledShape s;
-    s.tiles_x = (nx + kTX - 1) / kTX;
-    s.tiles_y = (ny + kTY - 1) / kTY;
+    const TileDims td = tile_dims(tile);
+    s.tiles_x = (nx + td.tx - 1) / td.tx;
+    s.tiles_y = (ny + td.ty - 1) / td.ty;
     const long long C = (long long)nprob * s.tiles_x * s.tiles_y;
     s.zchunk = zchunk > 0 ? (zchunk < nz ? zchunk : nz) : 0;
     if (s.zchunk > 0) {
         s.grid = (int)(C * ((nz + s.zchunk - 1) / s.zchunk));
         s.per_cta = 0;
     } else {
-        s.grid = tiled_grid_size() * (sizeof(T) == 4 ? kMinBlocks : 1);
+        s.grid = tiled_grid_size() * tile_min_blocks<T>(tile);
         // plane steps per CTA in the second phase (columns left after whole rounds)
         const long long rem = (C - (C / s.grid) * s.grid) * nz;
         s.per_cta = (rem + s.grid - 1) / s.grid;
@@ -660,13 +696,14 @@ inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1, int zchunk 
     return s;
 }
 
-// Schedules the autotuner tries: persistent, and plane chunks giving about 3..8 CTAs of
-// work per resident CTA slot.
-inline int tiled_candidates(int nx, int ny, int nz, int nprob, int out[8]) {
+// Schedules the autotuner tries for a tile shape: persistent, and plane chunks giving
+// about 3..8 CTAs of work per resident CTA slot.
+inline int tiled_candidates(int nx, int ny, int nz, int nprob, int out[8], int tile = 0) {
     int n = 0;
     out[n++] = 0;
-    const long long C = (long long)nprob * ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY);
-    const long long slots = (long long)tiled_grid_size() * kMinBlocks;
+    const TileDims td = tile_dims(tile);
+    const long long C = (long long)nprob * ((nx + td.tx - 1) / td.tx) * ((ny + td.ty - 1) / td.ty);
+    const long long slots = (long long)tiled_grid_size() * tile_min_blocks<float>(tile);
     for (int w = 3; w <= 8 && n < 8; ++w) {
         long long chunks = (w * slots + C - 1) / C;
         if (chunks < 1) chunks = 1;
@@ -690,32 +727,36 @@ inline bool tiled_supported(int nx, int ny, int nz, int nprob) {
 
 // Number of reduction partials per drive written by one launch (one per CTA).
 template <typename T>
-inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob, int zchunk = 0) {
-    return tiled_shape<T>(nx, ny, nz, nprob, zchunk).grid;
+inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob, int zchunk = 0, int tile = 0) {
+    return tiled_shape<T>(nx, ny, nz, nprob, zchunk, tile).grid;
 }
 
-// Largest grid over the autotuner's candidates (sizes the reduction buffers).
+// Largest grid over the autotuner's candidates of every tile shape (sizes the
+// reduction buffers).
 template <typename T>
 inline long long tiled_max_blocks(int nx, int ny, int nz, int nprob) {
-    int cand[8];
-    const int n = tiled_candidates(nx, ny, nz, nprob, cand);
     long long g = 0;
-    for (int i = 0; i < n; ++i) {
-        const long long b = tiled_num_blocks<T>(nx, ny, nz, nprob, cand[i]);
-        g = b > g ? b : g;
+    for (int t = 0; t < tile_count<T>(); ++t) {
+        int cand[8];
+        const int n = tiled_candidates(nx, ny, nz, nprob, cand, t);
+        for (int i = 0; i < n; ++i) {
+            const long long b = tiled_num_blocks<T>(nx, ny, nz, nprob, cand[i], t);
+            g = b > g ? b : g;
+        }
     }
     return g;
 }
 
-template <typename T, int MODE, bool RED, bool SRC, bool ALPHA>
-inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, cudaStream_t s) {
-    TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk);
+template <typename T, class C, int MODE, bool RED, bool SRC, bool ALPHA>
+inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, int tile,
+                                  cudaStream_t s) {
+    TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk, tile);
     if (B.multi) {
         const SweepProblem<T> &L = B.prob[B.nprob - 1];
         sh.grid = (int)(L.unit_begin + (long long)L.tiles_x * L.tiles_y * ((L.nz + L.zchunk - 1) / L.zchunk));
     }
-    const size_t smem = sizeof(TiledSmem<T>);
-    auto kern = sweep_tiled_kernel<T, MODE, RED, SRC, ALPHA>;
+    const size_t smem = sizeof(TiledSmem<T, C>);
+    auto kern = sweep_tiled_kernel<T, C, MODE, RED, SRC, ALPHA>;
     // the shared-memory attributes are per device: one bit per device and instantiation
     static std::atomic<unsigned long long> attr_set{0};
     const int dev = current_device();
@@ -727,33 +768,57 @@ inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, 
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(bit, std::memory_order_acq_rel);
     }
-    kern<<<sh.grid, kNT, smem, s>>>(B, code, sh.tiles_x, sh.tiles_y, sh.per_cta, sh.zchunk);
+    kern<<<sh.grid, C::NT, smem, s>>>(B, code, sh.tiles_x, sh.tiles_y, sh.per_cta, sh.zchunk);
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
-inline cudaError_t launch_tiled_m(const SweepBatch<T> &B, const uint32_t *code, bool red, bool src, int zc,
+template <typename T, class C, int MODE>
+inline cudaError_t launch_tiled_m(const SweepBatch<T> &B, const uint32_t *code, bool red, bool src, int zc, int tile,
                                   cudaStream_t s) {
     const bool alpha = B.alpha != nullptr;
     if (red) {
-        if (src) return alpha ? launch_tiled_t<T, MODE, true, true, true>(B, code, zc, s)
-                              : launch_tiled_t<T, MODE, true, true, false>(B, code, zc, s);
-        return alpha ? launch_tiled_t<T, MODE, true, false, true>(B, code, zc, s)
-                     : launch_tiled_t<T, MODE, true, false, false>(B, code, zc, s);
+        if (src) return alpha ? launch_tiled_t<T, C, MODE, true, true, true>(B, code, zc, tile, s)
+                              : launch_tiled_t<T, C, MODE, true, true, false>(B, code, zc, tile, s);
+        return alpha ? launch_tiled_t<T, C, MODE, true, false, true>(B, code, zc, tile, s)
+                     : launch_tiled_t<T, C, MODE, true, false, false>(B, code, zc, tile, s);
     }
-    if (src) return alpha ? launch_tiled_t<T, MODE, false, true, true>(B, code, zc, s)
-                          : launch_tiled_t<T, MODE, false, true, false>(B, code, zc, s);
-    return alpha ? launch_tiled_t<T, MODE, false, false, true>(B, code, zc, s)
-                 : launch_tiled_t<T, MODE, false, false, false>(B, code, zc, s);
+    if (src) return alpha ? launch_tiled_t<T, C, MODE, false, true, true>(B, code, zc, tile, s)
+                          : launch_tiled_t<T, C, MODE, false, true, false>(B, code, zc, tile, s);
+    return alpha ? launch_tiled_t<T, C, MODE, false, false, true>(B, code, zc, tile, s)
+                 : launch_tiled_t<T, C, MODE, false, false, false>(B, code, zc, tile, s);
 }
 
-template <typename T>
-inline int launch_tiled(const SweepBatch<T> &B, const uint32_t *code, int mode, bool red, bool src, int zchunk,
-                        cudaStream_t s) {
-    cudaError_t e;
-    if (mode == kModeU) e = launch_tiled_m<T, kModeU>(B, code, red, src, zchunk, s);
-    else if (mode == kModePU) e = launch_tiled_m<T, kModePU>(B, code, red, src, zchunk, s);
-    else e = launch_tiled_m<T, kModeP>(B, code, red, src, zchunk, s);
+template <typename T, class C>
+inline cudaError_t launch_tiled_c(const SweepBatch<T> &B, const uint32_t *code, int mode, bool red, bool src,
+                                  int zchunk, int tile, cudaStream_t s) {
+    if (mode == kModeU) return launch_tiled_m<T, C, kModeU>(B, code, red, src, zchunk, tile, s);
+    if (mode == kModePU) return launch_tiled_m<T, C, kModePU>(B, code, red, src, zchunk, tile, s);
+    return launch_tiled_m<T, C, kModeP>(B, code, red, src, zchunk, tile, s);
+}
+
+// Per-shape launchers, each compiled in its own translation unit (pm_sweep_*.cu).
+cudaError_t launch_tiled_f32_t0(const SweepBatch<float> &B, const uint32_t *code, int mode, bool red, bool src,
+                                int zchunk, cudaStream_t s);
+cudaError_t launch_tiled_f32_t1(const SweepBatch<float> &B, const uint32_t *code, int mode, bool red, bool src,
+                                int zchunk, cudaStream_t s);
+cudaError_t launch_tiled_f32_t2(const SweepBatch<float> &B, const uint32_t *code, int mode, bool red, bool src,
+                                int zchunk, cudaStream_t s);
+cudaError_t launch_tiled_f64_t0(const SweepBatch<double> &B, const uint32_t *code, int mode, bool red, bool src,
+                                int zchunk, cudaStream_t s);
+
+// One sweep launch with tile shape `tile` (0: 64 x 12, two cells per thread; 1: 64 x 12,
+// four cells per thread; 2: 64 x 8, four cells per thread); FP64 fields use shape 0 (the
+// FP64 kernel is bound by the FP64 rate).  Returns a pm_status.
+inline int launch_tiled(const SweepBatch<float> &B, const uint32_t *code, int mode, bool red, bool src, int zchunk,
+                        cudaStream_t s, int tile = 0) {
+    const cudaError_t e = tile == 1   ? launch_tiled_f32_t1(B, code, mode, red, src, zchunk, s)
+                          : tile == 2 ? launch_tiled_f32_t2(B, code, mode, red, src, zchunk, s)
+                                      : launch_tiled_f32_t0(B, code, mode, red, src, zchunk, s);
+    return e == cudaSuccess ? 0 : (e == cudaErrorMemoryAllocation ? 6 : 7);
+}
+inline int launch_tiled(const SweepBatch<double> &B, const uint32_t *code, int mode, bool red, bool src, int zchunk,
+                        cudaStream_t s, int = 0) {
+    const cudaError_t e = launch_tiled_f64_t0(B, code, mode, red, src, zchunk, s);
     return e == cudaSuccess ? 0 : (e == cudaErrorMemoryAllocation ? 6 : 7);
 }
 

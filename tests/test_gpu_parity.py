@@ -249,24 +249,44 @@ def test_divergence_and_iteration_limit_are_reported(api):
     assert bool(torch.isfinite(r["u"]).all())
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3])
 @pytest.mark.parametrize("schedule", [-1, 1, 2, 5, 13, 40])
-@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1)], ids=["periodic", "walls_xz"])
-def test_schedules_give_identical_fields(api, schedule, bc):
-    """Every work split of the tiled kernel (persistent CTAs, plane chunks of any length,
-    including chunks shorter than the kernel's pipeline) does the same arithmetic per
-    cell: the fields after 11 iterations are bit-identical to the default schedule's."""
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1), (0, 1, 0)], ids=["periodic", "walls_xz", "walls_y"])
+def test_tiles_and_schedules_give_identical_fields(api, tile, schedule, bc):
+    """Every tile shape (64 x 12 cells with two or four cells per thread, 64 x 8 with four)
+    and every work split (persistent CTAs, plane chunks of any length, including chunks
+    shorter than the kernel's pipeline) does the same arithmetic per cell: the fields
+    after 11 iterations are bit-identical to the default shape and split.  The domain has
+    ragged tiles in x and y."""
     mask = G.overlapping_spheres((27, 19, 72), 3.0, 0.6, seed=21)
     ref = _gpu_iterate(api, mask, 11, 1, "fp32", bc=bc)
-    got = _gpu_iterate(api, mask, 11, 1, "fp32", bc=bc, schedule=schedule)
+    got = _gpu_iterate(api, mask, 11, 1, "fp32", bc=bc, schedule=schedule, tile=tile)
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+
+
+@pytest.mark.parametrize("tile", [2, 3])
+def test_tiles_with_source_and_drag_terms(api, tile):
+    """The source (defect-correction) and drag (adjoint) variants of the wide shapes
+    against the first shape: the defect-corrected tensor and the tensor with a drag field
+    agree to the convergence noise of the window criterion."""
+    mask = G.overlapping_spheres((20, 24, 28), 3.0, 0.6, seed=12)
+    a = api.permeability_tensor(mask, tol=1e-11, precision="dc64", tile=1)
+    b = api.permeability_tensor(mask, tol=1e-11, precision="dc64", tile=tile)
+    assert b["stats"][0]["tile"] == tile
+    np.testing.assert_allclose(b["k_raw"], a["k_raw"], rtol=1e-7, atol=1e-12)
+    alpha = torch.from_numpy(G.rng(5).random(mask.shape) * 0.5).float().cuda()
+    ka = api.sensitivity(mask, None, alpha=alpha, tol=1e-9, tile=1)["k_raw"]
+    kb = api.sensitivity(mask, None, alpha=alpha, tol=1e-9, tile=tile)["k_raw"]
+    np.testing.assert_allclose(kb, ka, rtol=1e-6, atol=1e-10)
 
 
 def test_schedule_reported_and_converged_k_unchanged(api):
     mask = G.overlapping_spheres((40, 24, 32), 3.0, 0.6, seed=22)
     d = torch.from_numpy(mask).cuda()
-    a = api.solve_direction(d, 0, fields=False, tol=1e-7, schedule=-1)
-    b = api.solve_direction(d, 0, fields=False, tol=1e-7, schedule=7)
+    a = api.solve_direction(d, 0, fields=False, tol=1e-7, schedule=-1, tile=1)
+    b = api.solve_direction(d, 0, fields=False, tol=1e-7, schedule=7, tile=1)
     assert a["stats"]["schedule"] == -1 and b["stats"]["schedule"] == 7
+    assert a["stats"]["tile"] == 1 and b["stats"]["tile"] == 1
     assert a["stats"]["iters"] == b["stats"]["iters"]
     np.testing.assert_allclose(a["k_col"], b["k_col"], rtol=1e-12, atol=1e-14)
 
@@ -294,8 +314,8 @@ def test_config2_full_size_fields_after_21_iterations(api, oracle_mod, drive_dir
     np.testing.assert_allclose(pg, po, rtol=0, atol=2e-5 * np.abs(po).max())
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_persistent_rounds_trajectory(api, oracle_mod, precision):
+@pytest.mark.parametrize("precision,tile", [("fp32", 1), ("fp32", 2), ("fp32", 3), ("fp64", 1)])
+def test_persistent_rounds_trajectory(api, oracle_mod, precision, tile):
     """1024 x 640 x 6 cells make 16 x 54 = 864 tile columns, more than the persistent
     grid (2 CTAs per SM for FP32, 1 for FP64): whole-column rounds in lockstep run
     before the equal plane ranges of the remaining columns.  Element-wise parity with
@@ -305,7 +325,7 @@ def test_persistent_rounds_trajectory(api, oracle_mod, precision):
     tol = 1e-11 if precision == "fp64" else 2e-5
     for n in (1, 2, 10):
         for drive_dir in (0, 1):
-            Ug, pg = _gpu_iterate(api, mask, n, drive_dir, precision, schedule=-1)
+            Ug, pg = _gpu_iterate(api, mask, n, drive_dir, precision, schedule=-1, tile=tile)
             Uo, po = _oracle_iterate(oracle_mod, mask, n, drive_dir, dt=dt)
             np.testing.assert_allclose(Ug, Uo, rtol=0, atol=tol * np.abs(Uo).max(), err_msg=f"u n={n}")
             np.testing.assert_allclose(pg, po, rtol=0, atol=tol * np.abs(po).max(), err_msg=f"p n={n}")
