@@ -129,8 +129,13 @@ typedef struct pm_options {
                                  choice when autotune is set, else 1); 1 = 64 x 12 cells,
                                  two per thread; 2 = 64 x 12, four per thread; 3 = 64 x 8,
                                  four per thread (FP32 fields; FP64 fields always use 1).
-                                 Every shape gives the same fields, bit for bit. */
-    int32_t reserved[5];
+                                 Every shape gives the same fields, bit for bit.  (The
+                                 transposed sweep of adjoint solves has its own shape,
+                                 reported as 4.) */
+    int32_t sequence;         /* pm_batch_ktensor: 0 = every (domain, drive) problem in each
+                                 sweep launch; 1 = the domains in order, each starting from
+                                 the converged fields of the previous one (same size) */
+    int32_t reserved[4];
 } pm_options;
 
 typedef struct pm_stats {
@@ -246,9 +251,13 @@ PM_API int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_o
  * sequence, Sec. 7.3, and cropped sub-domains of uneven sizes): every (domain, drive)
  * problem of Eq. (cases_pressure) is a member of each sweep launch, the windows run as one
  * captured CUDA graph, and each problem stops sweeping when its criterion holds.  Problems
- * are processed in groups of up to 64.
- *   doms: host array of n_domains domains; every nx must be a multiple of 4 and all
- *   domains must share the boundary conditions (else PM_ERR_UNSUPPORTED).
+ * are processed in groups of up to 64.  With opt->sequence = 1 the domains are solved one
+ * after another instead (their drives batched), each starting from the converged fields of
+ * the previous domain when the two have the same size.
+ *   doms: host array of n_domains domains sharing the boundary conditions (else
+ *   PM_ERR_UNSUPPORTED).  An x extent that is not a multiple of 4 is handled inside: a
+ *   periodic x axis is repeated 2 or 4 times (the same discrete problem), a wall x axis
+ *   padded with solid columns; k and the statistics refer to the domain as given.
  *   drives: host, n_domains bit masks (bit j = drive along e_(j+1)), or NULL / 0 for all.
  *   k_out: host, 9 doubles per domain (row-major, symmetrised); k_raw: same, unsymmetrised,
  *   or NULL.  st: host, 3 pm_stats per domain (per drive), or NULL.
@@ -264,17 +273,26 @@ PM_API int pm_batch_ktensor(int n_domains, const pm_domain *doms, const int32_t 
  * the paper's problem).  Forward solves for every drive j with a nonzero column of w,
  * solves of the transposed system (viscous operator transposed) for every row i, then
  *   dJ/d alpha_c = -(dx^2 / (2 Re^2 N)) sum_ij w_ij sum_{faces F of c} v^(i)_F u^(j)_F
- * (u^(j), v^(i) in iteration units for a unit drive).
+ * (u^(j), v^(i) in iteration units for a unit drive).  FP32 fields run the transposed
+ * solves on the tiled kernel (four cells per thread); FP64 fields on the simple kernel.
  *   alpha: device, N floats, or NULL for 0.      w: host, 9 doubles, row-major.
  *   dJ_dalpha: device, N floats, caller-owned, written for every cell (dx^2 units of k);
- *   NULL: forward only -- the three drives are solved with alpha and k_raw is returned
- *   (w may then be NULL).
+ *   NULL: forward only -- the drives of the nonzero columns of w (all three when w is
+ *   NULL) are solved with alpha, and J and k_raw are returned.
  *   J (host, may be NULL): the objective.  k_raw (host, 9 or NULL): the forward columns.
+ *   u_fwd (host array of 3 device pointers, or NULL; NULL entries allowed): the forward
+ *   velocity fields u^(j) = [u_x | u_y | u_z] of drive j, 3N values in iteration units for
+ *   a unit drive (float for PM_FP32_RED64, double for PM_FP64).  fwd_given = 0: each
+ *   non-NULL entry of a solved drive receives its converged field.  fwd_given = 1: the
+ *   non-NULL entries hold converged fields from an earlier call on the same mask, alpha and
+ *   options (for example the forward pass of an autograd function), those drives are not
+ *   solved again and their k columns come from the given fields.
  *   Precision PM_FP32_RED64 or PM_FP64 (PM_FP32_DC64: PM_ERR_UNSUPPORTED).
- *   Errors: PM_ERR_INVALID_ARG (w all zero), PM_ERR_NO_FLUID, PM_ERR_NOT_CONVERGED,
+ *   Errors: PM_ERR_INVALID_ARG (w all zero, or dJ_dalpha without w), PM_ERR_NO_FLUID, PM_ERR_NOT_CONVERGED,
  *   PM_ERR_DIVERGED, PM_ERR_OOM, PM_ERR_CUDA. */
 PM_API int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *opt,
-                          float *dJ_dalpha, double *J, double k_raw[9], void *cuda_stream);
+                          float *dJ_dalpha, double *J, double k_raw[9], void *const u_fwd[3], int32_t fwd_given,
+                          void *cuda_stream);
 
 /* Pre-processing (Sec. 5 "Processing input data": mirroring for symmetric periodicity).
  * Writes the mask followed by its mirror image along every axis whose bit is set in axes

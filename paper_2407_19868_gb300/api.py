@@ -61,7 +61,7 @@ class Options(C.Structure):
                 ("c2", C.c_double), ("use_graph", C.c_int32), ("check_percolation", C.c_int32),
                 ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
                 ("autotune", C.c_int32), ("schedule", C.c_int32), ("tile", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("sequence", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -118,7 +118,8 @@ def load():
                                          vp, vp, vp, vp, dp, C.POINTER(Stats), vp]
         L.pm_permeability_tensor.argtypes = [C.POINTER(Domain), C.c_double, C.POINTER(Options), dp, dp,
                                              C.POINTER(Stats), vp]
-        L.pm_sensitivity.argtypes = [C.POINTER(Domain), vp, dp, C.POINTER(Options), vp, dp, dp, vp]
+        L.pm_sensitivity.argtypes = [C.POINTER(Domain), vp, dp, C.POINTER(Options), vp, dp, dp, C.POINTER(vp),
+                                     C.c_int32, vp]
         L.pm_batch_ktensor.argtypes = [C.c_int, C.POINTER(Domain), C.POINTER(C.c_int32), C.POINTER(Options), dp, dp,
                                        C.POINTER(Stats), vp]
         L.pm_principal_axes.argtypes = [dp, dp, dp]
@@ -307,10 +308,14 @@ def permeability_tensor(mask, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts
             "stats": [s[i].as_dict() for i in range(3)], "status": st}
 
 
-def sensitivity(mask, w=None, alpha=None, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts):
+def sensitivity(mask, w=None, alpha=None, dx: float = 1.0, bc=(0, 0, 0), stream=None, fwd=None,
+                keep_fwd=False, grad=True, **opts):
     """Adjoint sensitivity of J = sum w_ij k_ij to a per-cell drag alpha (pm_sensitivity).
     alpha: CUDA float32 tensor (nz, ny, nx) or None.  With w=None only the forward solves
-    run and dJ is None.  Returns dict(dJ, J, k_raw, status)."""
+    run and dJ is None.  fwd: forward fields from an earlier call (tensor (3, 3, nz, ny,
+    nx): drive, component; those drives are not solved again); keep_fwd: return this
+    call's forward fields as "fwd"; grad=False: no gradient, only the forward solves of
+    w's nonzero columns (J and those k columns).  Returns dict(dJ, J, k_raw, status, fwd)."""
     import torch
     m = _Mask(mask, dx=dx, bc=bc)
     o = options(**opts)
@@ -319,14 +324,26 @@ def sensitivity(mask, w=None, alpha=None, dx: float = 1.0, bc=(0, 0, 0), stream=
         a = alpha.detach().to(device="cuda", dtype=torch.float32).contiguous()
         if a.numel() != m.N:
             raise ValueError("alpha must have one value per voxel")
-    dJ = torch.empty(m.shape, dtype=torch.float32, device="cuda") if w is not None else None
+    dJ = torch.empty(m.shape, dtype=torch.float32, device="cuda") if w is not None and grad else None
     wa = (C.c_double * 9)(*np.asarray(w, dtype=np.float64).reshape(-1)) if w is not None else None
     J = C.c_double(0.0)
     kr = (C.c_double * 9)()
+    ftype = torch.float64 if o.precision == FP64 else torch.float32
+    given = 0
+    uf = None
+    if fwd is not None:
+        if fwd.dtype != ftype or not fwd.is_cuda or fwd.numel() != 9 * m.N:
+            raise ValueError("fwd must be a CUDA tensor (3, 3, nz, ny, nx) of the precision's type")
+        uf, given = fwd.contiguous(), 1
+    elif keep_fwd:
+        uf = torch.zeros((3, 3) + tuple(m.shape), dtype=ftype, device="cuda")
+    ptrs = (C.c_void_p * 3)(*([uf[j].data_ptr() for j in range(3)] if uf is not None else [None] * 3))
     st = load().pm_sensitivity(C.byref(m.dom), a.data_ptr() if a is not None else None, wa, C.byref(o),
-                               dJ.data_ptr() if dJ is not None else None, C.byref(J), kr, _stream(stream))
+                               dJ.data_ptr() if dJ is not None else None, C.byref(J), kr,
+                               ptrs if uf is not None else None, given, _stream(stream))
     _check(st, "pm_sensitivity", soft=(PM_OK, PM_ERR_NOT_CONVERGED))
-    return {"dJ": dJ, "J": float(J.value), "k_raw": np.array(kr[:]).reshape(3, 3), "status": st}
+    return {"dJ": dJ, "J": float(J.value), "k_raw": np.array(kr[:]).reshape(3, 3), "status": st,
+            "fwd": uf if keep_fwd else None}
 
 
 def batch_ktensor(masks, drives=None, dx: float = 1.0, bc=(0, 0, 0), stream=None, **opts):
@@ -352,23 +369,24 @@ def _ktensor_fn():
 
     class KTensorFn(torch.autograd.Function):
         """k_raw(alpha): the 3x3 permeability tensor of the mask with a per-cell drag
-        alpha (alpha = 0 is the paper's problem).  backward(grad_k) is one adjoint
-        solve: pm_sensitivity with w = grad_k gives d(sum grad_k * k)/d alpha."""
+        alpha (alpha = 0 is the paper's problem).  forward keeps the three forward fields;
+        backward(grad_k) runs only the transposed solves: pm_sensitivity with w = grad_k
+        and the kept fields gives d(sum grad_k * k)/d alpha."""
 
         @staticmethod
         def forward(ctx, alpha, mask, opts):
-            r = sensitivity(mask, None, alpha=alpha, **opts)
+            r = sensitivity(mask, None, alpha=alpha, keep_fwd=True, **opts)
             ctx.mask, ctx.opts = mask, opts
-            ctx.save_for_backward(alpha)
+            ctx.save_for_backward(alpha, r["fwd"])
             return torch.as_tensor(r["k_raw"], dtype=torch.float64, device=alpha.device)
 
         @staticmethod
         def backward(ctx, grad_k):
-            (alpha,) = ctx.saved_tensors
+            alpha, fwd = ctx.saved_tensors
             w = grad_k.detach().double().cpu().numpy()
             if not np.any(w):
                 return torch.zeros_like(alpha), None, None
-            r = sensitivity(ctx.mask, w, alpha=alpha, **ctx.opts)
+            r = sensitivity(ctx.mask, w, alpha=alpha, fwd=fwd, **ctx.opts)
             return r["dJ"].to(alpha.dtype), None, None
 
     return KTensorFn

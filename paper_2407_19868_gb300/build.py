@@ -8,7 +8,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
-SOURCES = ["pm_api.cu", "pm_sweep_f32_t0.cu", "pm_sweep_f32_t1.cu", "pm_sweep_f32_t2.cu", "pm_sweep_f64_t0.cu"]
+SOURCES = ["pm_api.cu", "pm_sweep_f32_t0.cu", "pm_sweep_f32_t1.cu", "pm_sweep_f32_t2.cu", "pm_sweep_f64_t0.cu",
+           "pm_sweep_f32_tr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -198,7 +198,18 @@ struct Geometry {
     const uint8_t *mask = nullptr;  // device copy of the mask (or the caller's device mask)
     uint8_t *flags = nullptr;   // device, one byte per cell (simple kernel)
     uint32_t *code = nullptr;   // device, one stencil code word per cell (tiled kernel)
+    uint32_t *tcode = nullptr;  // device, two transposed code words per cell (adjoint, on demand)
 };
+
+// Transposed stencil codes of a geometry (the tiled transposed sweep of adjoint solves).
+int build_tcode(Geometry &g, cudaStream_t s, Scratch &scr) {
+    int st = scr.alloc(&g.tcode, (size_t)(2 * g.N));
+    if (st) return st;
+    tcode_kernel<<<launch_grid(g.N), 256, 0, s>>>(g.code, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.tcode);
+    note_launch();
+    PM_CK(cudaGetLastError());
+    return PM_OK;
+}
 
 // Fixed-pressure axis of a domain, -1 if none.
 int pressure_axis(const pm_domain *dom) {
@@ -524,6 +535,7 @@ struct Solver {
     long long total_units = 0;
     double t_setup = 0.0;  // host seconds from the entry point to the first sweep
     bool capturing = false;  // launches go into a graph (counted when it is replayed)
+    bool tuned = false;      // tile shape and split chosen (tune() ran once)
     const Geometry &G(int k) const { return multi ? *geo[k] : g; }
 
     Solver(const Geometry &gg, const pm_options &oo, cudaStream_t ss, Scratch &sc)
@@ -551,6 +563,14 @@ struct Solver {
                 const long long b = tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, zchunk, t);
                 nblk_t = b > nblk_t ? b : nblk_t;
             }
+        if (transposed) {
+            tile = kTileTR;
+            int cand[8];
+            const int n = tiled_candidates(g.nx, g.ny, g.nz, np, cand, kTileTR);
+            for (int i = 0; i < n; ++i)
+                nblk_t = std::max(nblk_t, tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, cand[i], kTileTR));
+            if (zchunk > 0) nblk_t = std::max(nblk_t, tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, zchunk, kTileTR));
+        }
         const long long nblk_max = nblk > nblk_t ? nblk : nblk_t;
         int st;
         for (int k = 0; k < nprob; ++k) {
@@ -631,6 +651,7 @@ struct Solver {
         B.N = g.N;
         B.flags = g.flags;
         B.code = g.code;
+        B.tcode = g.tcode;
         B.alpha = alpha;
         B.inv_re = inv_re;
         B.dt = dt;
@@ -683,7 +704,8 @@ struct Solver {
 
     bool use_tiled() const {
         if (multi) return true;  // batches are built only from tiled-kernel shapes
-        return o.kernel == 0 && !transposed && g.pax < 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
+        if (transposed && (sizeof(T) != 4 || !g.tcode)) return false;  // FP64 adjoint: simple kernel
+        return o.kernel == 0 && g.pax < 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
     }
 
     // One sweep of the given mode; flips the ping-pong buffers.
@@ -692,7 +714,13 @@ struct Solver {
         bool has_src = false;
         for (int k = 0; k < nprob; ++k) has_src |= src[k] != nullptr;
         if (use_tiled()) {
-            int st = launch_tiled(B, g.code, mode, reduce, has_src, zchunk, s, tile);
+            int st;
+            if constexpr (sizeof(T) == 4) {
+                st = transposed ? launch_tiled_transposed(B, g.code, mode, reduce, zchunk, s)
+                                : launch_tiled(B, g.code, mode, reduce, has_src, zchunk, s, tile);
+            } else {
+                st = launch_tiled(B, g.code, mode, reduce, has_src, zchunk, s, tile);
+            }
             if (st) return st;
         } else if (mode == kModeU) {
             reduce ? launch_simple<kModeU, true>(B, has_src) : launch_simple<kModeU, false>(B, has_src);
@@ -739,7 +767,9 @@ struct Solver {
         static std::mutex mu;
         static std::vector<Entry> cache;
         const int dev = current_device();
-        std::vector<long long> key{multi ? 1 : 0, nprob, o.tile, o.schedule};
+        bool has_src = false;
+        for (int k = 0; k < nprob; ++k) has_src |= src[k] != nullptr;
+        std::vector<long long> key{multi ? 1 : 0, nprob, o.tile, o.schedule, transposed ? 1 : 0, has_src ? 1 : 0};
         for (int k = 0; k < (multi ? nprob : 1); ++k) {
             key.push_back(G(k).nx);
             key.push_back(G(k).ny);
@@ -756,8 +786,8 @@ struct Solver {
                 }
         }
         std::vector<std::pair<int, int>> cand;  // (tile, zchunk)
-        for (int t = 0; t < tile_count<T>(); ++t) {
-            if (o.tile > 0 && o.tile <= tile_count<T>() && t != o.tile - 1) continue;
+        for (int t = 0; t < (transposed ? kTileTR + 1 : tile_count<T>()); ++t) {
+            if (transposed ? t != kTileTR : (o.tile > 0 && o.tile <= tile_count<T>() && t != o.tile - 1)) continue;
             if (multi || o.schedule != 0) {
                 cand.push_back({t, multi ? 0 : zchunk});
                 continue;
@@ -859,6 +889,7 @@ struct RunCriterion {
     double ref[kMaxBatch] = {0, 0, 0, 0};
     bool stop_on_stall = false;
     long long max_iter = 0;
+    bool retune = false;  // run the autotuner again (the sweep variant changed)
 };
 
 // Runs the batch to convergence from the loaded state.  Returns a pm_status.
@@ -885,7 +916,9 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
     int rc = S.sweep(kModeU, false);
     if (rc) status = rc;
     iters = 1;
-    if (!rc && o.autotune && (o.schedule == 0 || o.tile == 0)) iters += S.tune();
+    if (!rc && o.autotune && (o.schedule == 0 || o.tile == 0) && (!crit || crit->retune || !S.tuned))
+        iters += S.tune();
+    S.tuned = true;
     bool done = status != PM_OK;
     bool use_graph = o.use_graph != 0;
     if (!done && use_graph) {
@@ -1071,6 +1104,9 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
         }
         PM_CK(cudaGetLastError());
         std::memset(rs, 0, sizeof(rs));
+        // the correction sweeps also read the source: their best tile shape and split are
+        // tuned on their own (in the first round, as iterations of that round)
+        c2.retune = rounds == 1;
         status = run_to_convergence<float>(S, rs, t0, &c2);
         if (status != PM_OK && status != PM_ERR_NOT_CONVERGED) break;
         iters += rs[0].iters;
@@ -1393,7 +1429,8 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
 // transposed solves for the rows i, then the face products (sensitivity_kernel).
 template <typename T>
 int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *o,
-                     float *dJ, double *J, double *k_raw, cudaStream_t s, Scratch &scr, double t0) {
+                     float *dJ, double *J, double *k_raw, void *const u_fwd[3], int fwd_given, cudaStream_t s,
+                     Scratch &scr, double t0) {
     Geometry g;
     int rc = build_geometry(dom, s, scr, g);
     if (rc) return rc;
@@ -1411,26 +1448,34 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
             T *a = nullptr;
             if ((rc = scr.alloc(&a, (size_t)g.N))) return rc;
             scale_copy_kernel<T, float><<<launch_grid(g.N), 256, 0, s>>>(a, alpha, 1.0, g.N);
+            note_launch();
             PM_CK(cudaGetLastError());
             alpha_t = a;
         }
     }
-    int fdirs[3], nf = 0, adirs[3], na = 0;
+    // forward drives: every column j of w with a nonzero entry (all three when dJ is NULL);
+    // those whose fields the caller hands over are not solved again
+    int fdirs[3], nf = 0, gdirs[3], ng = 0, adirs[3], na = 0;
     for (int j = 0; j < 3; ++j) {
-        bool col = !dJ, row = false;  // forward only: all three drives, no adjoint
-        for (int i = 0; i < 3 && dJ; ++i) {
+        // no w: all three drives, forward only; no dJ: the drives of w's columns, forward only
+        bool col = !w, row = false;
+        for (int i = 0; i < 3 && w; ++i) {
             col |= w[3 * i + j] != 0.0;
-            row |= w[3 * j + i] != 0.0;
+            row |= dJ && w[3 * j + i] != 0.0;
         }
-        if (col) fdirs[nf++] = j;
+        if (col) {
+            if (fwd_given && u_fwd && u_fwd[j]) gdirs[ng++] = j;
+            else fdirs[nf++] = j;
+        }
         if (row) adirs[na++] = j;
     }
-    if (nf == 0) return PM_ERR_INVALID_ARG;
+    if (nf + ng == 0) return PM_ERR_INVALID_ARG;
+    if (na > 0 && sizeof(T) == 4 && o->kernel == 0 && (rc = build_tcode(g, s, scr))) return rc;
     Solver<T> F(g, *o, s, scr), A(g, *o, s, scr);
-    if ((rc = F.init(nf)) || (na > 0 && (rc = A.init(na)))) return rc;
+    A.transposed = true;
+    if ((nf > 0 && (rc = F.init(nf))) || (na > 0 && (rc = A.init(na)))) return rc;
     F.alpha = alpha_t;
     A.alpha = alpha_t;
-    A.transposed = true;
     for (int k = 0; k < nf; ++k) {
         F.dir[k] = fdirs[k];
         F.force[k] = 1.0;
@@ -1442,8 +1487,11 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
     pm_stats sf[kMaxBatch], sa[kMaxBatch];
     std::memset(sf, 0, sizeof(sf));
     std::memset(sa, 0, sizeof(sa));
-    int st = run_to_convergence<T>(F, sf, t0);
-    if (st != PM_OK && st != PM_ERR_NOT_CONVERGED) return st;
+    int st = PM_OK;
+    if (nf > 0) {
+        st = run_to_convergence<T>(F, sf, t0);
+        if (st != PM_OK && st != PM_ERR_NOT_CONVERGED) return st;
+    }
     if (na > 0) {
         int st2 = run_to_convergence<T>(A, sa, t0);
         if (st2 != PM_OK && st2 != PM_ERR_NOT_CONVERGED) return st2;
@@ -1451,9 +1499,31 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
     }
     SensArgs<T> args{};
     double kr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double dx2 = dom->voxel_size * dom->voxel_size;
     for (int k = 0; k < nf; ++k) {
-        args.fwd[fdirs[k]] = F.F[k].u[F.F[k].cur];
-        for (int i = 0; i < 3; ++i) kr[3 * i + fdirs[k]] = sf[k].q[i] / o->Re * dom->voxel_size * dom->voxel_size;
+        const int j = fdirs[k];
+        args.fwd[j] = F.F[k].u[F.F[k].cur];
+        for (int i = 0; i < 3; ++i) kr[3 * i + j] = sf[k].q[i] / o->Re * dx2;
+        if (u_fwd && u_fwd[j] && !fwd_given)
+            PM_CK(cudaMemcpyAsync(u_fwd[j], args.fwd[j], sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
+    }
+    if (ng > 0) {
+        // mean velocities of the handed-over fields (Appendix C columns)
+        const int nb = tiled_grid_size() * 4;
+        double *part = nullptr, *dq = nullptr;
+        if ((rc = scr.alloc(&part, (size_t)ng * nb * 4)) || (rc = scr.alloc(&dq, (size_t)ng * 4))) return rc;
+        for (int k = 0; k < ng; ++k) {
+            args.fwd[gdirs[k]] = static_cast<const T *>(u_fwd[gdirs[k]]);
+            sum_u_kernel<T><<<nb, 256, 0, s>>>(args.fwd[gdirs[k]], g.N, part + (size_t)k * nb * 4);
+        }
+        reduce_partials_kernel<<<ng, 256, 0, s>>>(part, nb, g.N, dq);
+        note_launch(ng + 1);
+        PM_CK(cudaGetLastError());
+        double hq[3 * 4];
+        PM_CK(cudaMemcpyAsync(hq, dq, sizeof(double) * 4 * ng, cudaMemcpyDeviceToHost, s));
+        PM_CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < ng; ++k)
+            for (int i = 0; i < 3; ++i) kr[3 * i + gdirs[k]] = hq[4 * k + i] / o->Re * dx2;
     }
     for (int k = 0; k < na; ++k) args.adj[adirs[k]] = A.F[k].u[A.F[k].cur];
     double Jv = 0.0;
@@ -1463,10 +1533,11 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
             Jv += w[3 * i + j] * kr[3 * i + j];
         }
     // dk_ij/d alpha_c = -(1 / (2 Re^2 N)) sum_F v^(i)_F u^(j)_F  (unit drive), times dx^2
-    const double scale = -dom->voxel_size * dom->voxel_size / (2.0 * o->Re * o->Re * (double)g.N);
+    const double scale = -dx2 / (2.0 * o->Re * o->Re * (double)g.N);
     if (dJ) {
         sensitivity_kernel<T><<<launch_grid(g.N), 256, 0, s>>>(args, g.nx, g.ny, g.nz, g.per[0], g.per[1],
                                                               g.per[2], scale, dJ);
+        note_launch();
         PM_CK(cudaGetLastError());
     }
     PM_CK(cudaStreamSynchronize(s));
@@ -1476,14 +1547,55 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
     return st;
 }
 
-// Many geometries in one solve: every (domain, drive) problem is a member of each sweep
-// launch (one CTA per column chunk of each), windows are one captured graph, converged
-// problems are switched off through device flags.
+// Domain of an x extent that the tiled kernel takes (a multiple of 4): a periodic x axis
+// is repeated 2 or 4 times (the periodic extension is the same discrete problem: the
+// fixed point repeats and the mean velocities are unchanged); a wall x axis is padded with
+// solid columns (the mean over the padded box is N'/N times the mean over the domain).
+// The extended mask lives in scratch; *qscale converts mean velocities back, *rep counts
+// the copies.
+int extend_x(const pm_domain *dom, cudaStream_t s, Scratch &scr, pm_domain *out, double *qscale, int *rep) {
+    *out = *dom;
+    *qscale = 1.0;
+    *rep = 1;
+    if (dom->nx % 4 == 0) return PM_OK;
+    const bool periodic = dom->bc[0] == PM_BC_PERIODIC;
+    const int r = periodic ? (dom->nx % 2 == 0 ? 2 : 4) : 1;
+    const int nxo = periodic ? r * dom->nx : (dom->nx + 3) / 4 * 4;
+    const long long N = (long long)dom->nx * dom->ny * dom->nz, M = (long long)nxo * dom->ny * dom->nz;
+    const uint8_t *src = dom->mask;
+    int st;
+    if (!dom->mask_on_device) {
+        uint8_t *m = nullptr;
+        if ((st = scr.alloc(&m, (size_t)N))) return st;
+        PM_CK(cudaMemcpyAsync(m, dom->mask, (size_t)N, cudaMemcpyHostToDevice, s));
+        src = m;
+    }
+    uint8_t *ext = nullptr;
+    if ((st = scr.alloc(&ext, (size_t)M))) return st;
+    extend_x_kernel<<<launch_grid(M), 256, 0, s>>>(src, dom->nx, dom->ny, dom->nz, nxo, r, ext);
+    note_launch();
+    PM_CK(cudaGetLastError());
+    out->nx = nxo;
+    out->mask = ext;
+    out->mask_on_device = 1;
+    *qscale = periodic ? 1.0 : (double)M / (double)N;
+    *rep = r;
+    return PM_OK;
+}
+
+// Many geometries in one solve.  Batch mode: every (domain, drive) problem is a member of
+// each sweep launch (one CTA per column chunk of each), windows are one captured graph,
+// converged problems are switched off through device flags.  Sequence mode
+// (opt->sequence): the domains are solved in order, the drives of one domain batched in
+// each launch, and each domain starts from the converged fields of the one before it when
+// the two have the same size (a precipitation sequence, Sec. 7.3, changes little from one
+// image to the next); the fields are set to 0 where the new geometry has no fluid.
 template <typename T>
 int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_options *o, double *k_out,
                double *k_raw, pm_stats *st, cudaStream_t s, Scratch &scr, double t0) {
     const long long l0 = t_launches;
     std::vector<Geometry> geos((size_t)nd);
+    std::vector<double> qscale((size_t)nd, 1.0);
     struct Prob {
         int d, j;
     };
@@ -1494,8 +1606,11 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             k_out[9 * d + i] = 0.0;
             if (k_raw) k_raw[9 * d + i] = 0.0;
         }
-        int rc = build_geometry(&doms[d], s, scr, geos[(size_t)d]);
+        pm_domain ed;
+        int rep = 1;
+        int rc = extend_x(&doms[d], s, scr, &ed, &qscale[(size_t)d], &rep);
         if (rc) return rc;
+        if ((rc = build_geometry(&ed, s, scr, geos[(size_t)d]))) return rc;
         int perc[3] = {1, 1, 1}, wraps[3];
         long long n_pore = 0;
         if ((rc = percolation_device(geos[(size_t)d], o->check_percolation != 0, s, scr, &n_pore, wraps))) return rc;
@@ -1507,7 +1622,7 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             if (st) {
                 std::memset(&st[3 * d + j], 0, sizeof(pm_stats));
                 st[3 * d + j].percolates = perc[j];
-                st[3 * d + j].n_fluid = n_pore;
+                st[3 * d + j].n_fluid = n_pore / rep;
             }
             if (!(want & (1 << j))) continue;
             if (!perc[j]) {
@@ -1517,39 +1632,100 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             probs.push_back({d, j});
         }
     }
-    for (size_t g0 = 0; g0 < probs.size(); g0 += kMaxBatch) {
-        const int np = (int)std::min<size_t>(kMaxBatch, probs.size() - g0);
-        Solver<T> S(geos[(size_t)probs[g0].d], *o, s, scr);
-        S.multi = true;
-        for (int k = 0; k < np; ++k) {
-            S.geo[k] = &geos[(size_t)probs[g0 + k].d];
-            S.dir[k] = probs[g0 + k].j;
-            S.force[k] = 1.0;
+    // k column j of domain d from the converged mean velocities of problem k
+    auto record = [&](int d, int j, const pm_stats &b) {
+        const double dx2 = doms[d].voxel_size * doms[d].voxel_size;
+        for (int i = 0; i < 3; ++i) {
+            const double kij = qscale[(size_t)d] * b.q[i] / o->Re * dx2;  // Appendix C, column j
+            if (k_raw) k_raw[9 * d + 3 * i + j] = kij;
+            k_out[9 * d + 3 * i + j] += 0.5 * kij;
+            k_out[9 * d + 3 * j + i] += 0.5 * kij;
         }
-        int rc = S.init(np);
-        if (rc) return rc;
-        S.t_setup = now_s() - t0;
-        pm_stats bst[kMaxBatch];
-        std::memset(bst, 0, sizeof(bst));
-        rc = run_to_convergence<T>(S, bst, t0);
-        if (rc != PM_OK && rc != PM_ERR_NOT_CONVERGED) return rc;
-        if (rc == PM_ERR_NOT_CONVERGED && status == PM_OK) status = rc;
-        for (int k = 0; k < np; ++k) {
-            const int d = probs[g0 + k].d, j = probs[g0 + k].j;
-            const double dx2 = doms[d].voxel_size * doms[d].voxel_size;
-            for (int i = 0; i < 3; ++i) {
-                const double kij = bst[k].q[i] / o->Re * dx2;  // Appendix C, column j
-                if (k_raw) k_raw[9 * d + 3 * i + j] = kij;
-                k_out[9 * d + 3 * i + j] += 0.5 * kij;
-                k_out[9 * d + 3 * j + i] += 0.5 * kij;
+        if (st) {
+            const int perc = st[3 * d + j].percolates;
+            const long long nf = st[3 * d + j].n_fluid;
+            st[3 * d + j] = b;
+            for (int i = 0; i < 3; ++i) st[3 * d + j].q[i] *= qscale[(size_t)d];
+            st[3 * d + j].percolates = perc;
+            st[3 * d + j].n_fluid = nf;
+        }
+    };
+    if (o->sequence) {
+        // warm-start fields per drive (iteration units), from the previous domain
+        T *wu[3] = {nullptr, nullptr, nullptr}, *wp[3] = {nullptr, nullptr, nullptr};
+        bool warm[3] = {false, false, false};
+        long long wN = -1;
+        int wshape[3] = {0, 0, 0};
+        size_t pi = 0;
+        for (int d = 0; d < nd; ++d) {
+            const Geometry &g = geos[(size_t)d];
+            int dirs[3], np = 0;
+            while (pi < probs.size() && probs[pi].d == d) dirs[np++] = probs[pi++].j;
+            const bool same = g.nx == wshape[0] && g.ny == wshape[1] && g.nz == wshape[2];
+            if (!same) warm[0] = warm[1] = warm[2] = false;
+            if (np == 0) continue;
+            if (wN < 0) {
+                wN = g.N;
+                for (int j = 0; j < 3; ++j) {
+                    int rc;
+                    if ((rc = scr.alloc(&wu[j], (size_t)(3 * g.N))) || (rc = scr.alloc(&wp[j], (size_t)g.N))) return rc;
+                }
             }
-            if (st) {
-                const int perc = st[3 * d + j].percolates;
-                const long long nf = st[3 * d + j].n_fluid;
-                st[3 * d + j] = bst[k];
-                st[3 * d + j].percolates = perc;
-                st[3 * d + j].n_fluid = nf;
+            Solver<T> S(g, *o, s, scr);
+            int rc = S.init(np);
+            if (rc) return rc;
+            for (int k = 0; k < np; ++k) {
+                S.dir[k] = dirs[k];
+                S.force[k] = 1.0;
+                if (same && warm[dirs[k]] && (rc = S.load_state(k, wu[dirs[k]], wp[dirs[k]]))) return rc;
             }
+            S.t_setup = now_s() - t0;
+            pm_stats bst[kMaxBatch];
+            std::memset(bst, 0, sizeof(bst));
+            rc = run_to_convergence<T>(S, bst, t0);
+            if (rc != PM_OK && rc != PM_ERR_NOT_CONVERGED) return rc;
+            if (rc == PM_ERR_NOT_CONVERGED && status == PM_OK) status = rc;
+            for (int k = 0; k < np; ++k) record(d, dirs[k], bst[k]);
+            // keep this domain's fields for the next one (same size only)
+            if (g.N <= wN) {
+                for (int k = 0; k < np; ++k) {
+                    const int j = dirs[k];
+                    PM_CK(cudaMemcpyAsync(wu[j], S.F[k].u[S.F[k].cur], sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
+                    PM_CK(cudaMemcpyAsync(wp[j], S.F[k].p[S.F[k].cur], sizeof(T) * g.N, cudaMemcpyDeviceToDevice, s));
+                    warm[j] = true;
+                }
+                for (int j = 0; j < 3; ++j) {
+                    bool solved = false;
+                    for (int k = 0; k < np; ++k) solved |= dirs[k] == j;
+                    if (!solved) warm[j] = false;
+                }
+                wshape[0] = g.nx;
+                wshape[1] = g.ny;
+                wshape[2] = g.nz;
+            } else {
+                warm[0] = warm[1] = warm[2] = false;
+                wshape[0] = wshape[1] = wshape[2] = 0;
+            }
+        }
+    } else {
+        for (size_t g0 = 0; g0 < probs.size(); g0 += kMaxBatch) {
+            const int np = (int)std::min<size_t>(kMaxBatch, probs.size() - g0);
+            Solver<T> S(geos[(size_t)probs[g0].d], *o, s, scr);
+            S.multi = true;
+            for (int k = 0; k < np; ++k) {
+                S.geo[k] = &geos[(size_t)probs[g0 + k].d];
+                S.dir[k] = probs[g0 + k].j;
+                S.force[k] = 1.0;
+            }
+            int rc = S.init(np);
+            if (rc) return rc;
+            S.t_setup = now_s() - t0;
+            pm_stats bst[kMaxBatch];
+            std::memset(bst, 0, sizeof(bst));
+            rc = run_to_convergence<T>(S, bst, t0);
+            if (rc != PM_OK && rc != PM_ERR_NOT_CONVERGED) return rc;
+            if (rc == PM_ERR_NOT_CONVERGED && status == PM_OK) status = rc;
+            for (int k = 0; k < np; ++k) record(probs[g0 + k].d, probs[g0 + k].j, bst[k]);
         }
     }
     if (st)
@@ -1832,7 +2008,8 @@ int pm_solve_direction(const pm_domain *dom, int dir, double drive, const pm_opt
 }
 
 int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], const pm_options *o,
-                   float *dJ_dalpha, double *J, double k_raw[9], void *cuda_stream) {
+                   float *dJ_dalpha, double *J, double k_raw[9], void *const u_fwd[3], int32_t fwd_given,
+                   void *cuda_stream) {
     int rc = validate_domain(dom);
     if (rc) return rc;
     if ((rc = validate_options(o))) return rc;
@@ -1844,9 +2021,9 @@ int pm_sensitivity(const pm_domain *dom, const float *alpha, const double w[9], 
     {
         Scratch scr(ss.s);
         if (o->precision == PM_FP64)
-            rc = sensitivity_impl<double>(dom, alpha, w, o, dJ_dalpha, J, k_raw, ss.s, scr, t0);
+            rc = sensitivity_impl<double>(dom, alpha, w, o, dJ_dalpha, J, k_raw, u_fwd, fwd_given, ss.s, scr, t0);
         else
-            rc = sensitivity_impl<float>(dom, alpha, w, o, dJ_dalpha, J, k_raw, ss.s, scr, t0);
+            rc = sensitivity_impl<float>(dom, alpha, w, o, dJ_dalpha, J, k_raw, u_fwd, fwd_given, ss.s, scr, t0);
     }
     cudaError_t e = cudaStreamSynchronize(ss.s);
     if (rc == PM_OK && e != cudaSuccess) rc = map_cuda(e);
@@ -1861,7 +2038,7 @@ int pm_batch_ktensor(int n_domains, const pm_domain *doms, const int32_t *drives
     if (o->precision == PM_FP32_DC64) return PM_ERR_UNSUPPORTED;
     for (int d = 0; d < n_domains; ++d) {
         if ((rc = validate_domain(&doms[d]))) return rc;
-        if (doms[d].nx % 4 != 0 || pressure_axis(&doms[d]) >= 0) return PM_ERR_UNSUPPORTED;
+        if (pressure_axis(&doms[d]) >= 0) return PM_ERR_UNSUPPORTED;
         for (int a = 0; a < 3; ++a)
             if (doms[d].bc[a] != doms[0].bc[a]) return PM_ERR_UNSUPPORTED;
         if (drives && (drives[d] < 0 || drives[d] > 7)) return PM_ERR_INVALID_ARG;

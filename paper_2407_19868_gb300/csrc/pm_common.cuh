@@ -36,6 +36,19 @@ __host__ __device__ constexpr int code_shift(int d, int i) {
     return node_shift(d) + (i == (d == 0 ? 1 : 0) ? 0 : 3);
 }
 
+// Transposed stencil code of a cell (adjoint solves; tcode_kernel), two words per cell.
+// The transpose of the wall stencil gathers, for node a along axis i, the coefficients
+// that its neighbours b = a + m e_i (|m| <= 2) apply to a.  Per node u_d and
+// perpendicular axis i an 8-bit slot (slot index tslot(d, i), word slot / 4, bit
+// 8 (slot % 4)):
+//   bits 0-1  wall kind of a itself (its diagonal coefficient)
+//   bits 2-3  wall kind of the node at -1 (its coefficient on a, which is its
+//             coefficient on both of its +-1 neighbours)
+//   bits 4-5  wall kind of the node at +1
+//   bit 6     the node at -2 is a case 4/5 node whose far node is +2 (coefficient -1/5)
+//   bit 7     the node at +2 is a case 4/5 node whose far node is -2 (coefficient -1/5)
+__host__ __device__ constexpr int tslot(int d, int i) { return 2 * d + (i == (d == 0 ? 1 : 0) ? 0 : 1); }
+
 // Sweep variants.  The fused sweep works on the staggered state (u^n, p^{n-1}): it first
 // forms p^n = p^{n-1} - dt c^2 (D u^n - r_p) on the cells it needs, then
 // u^{n+1} = u^n + dt R_u(u^n, p^n).  This is exactly the paper's order (velocity update,
@@ -77,6 +90,7 @@ struct SweepBatch {
     long long N;
     const uint8_t *flags;  // N
     const uint32_t *code;  // N stencil codes (wall cases), used by the transposed sweep
+    const uint32_t *tcode; // [N][2] transposed stencil codes (tiled transposed sweep)
     const T *alpha;        // N per-cell drag or nullptr
     T inv_re, dt, dtc2;
     int nprob;

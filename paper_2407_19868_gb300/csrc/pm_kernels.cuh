@@ -55,6 +55,21 @@ __global__ void mirror_kernel(const uint8_t *__restrict__ in, int nx, int ny, in
     }
 }
 
+// Width extension of a mask for the tiled kernel (x extent a multiple of 4): the first
+// rep * nx columns of out repeat the mask periodically (a periodic x axis, where the
+// repeated domain has the same fixed point), the remaining columns up to nxo are solid
+// (a wall x axis, where outside the box counts as solid anyway).
+__global__ void extend_x_kernel(const uint8_t *__restrict__ in, int nx, int ny, int nz, int nxo, int rep,
+                                uint8_t *__restrict__ out) {
+    const long long M = (long long)nxo * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < M;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nxo);
+        const long long r = c / nxo;
+        out[c] = x < rep * nx ? in[(long long)(x % nx) + (long long)nx * r] : (uint8_t)1;
+    }
+}
+
 // Zero the values on non-fluid faces and solid cells (the invariant every sweep relies
 // on), used on caller-provided starting fields.
 template <typename T>
@@ -121,6 +136,45 @@ __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, in
             }
         }
         code[c] = w;
+    }
+}
+
+// Transposed stencil codes (layout: tslot in pm_common.cuh) from the stencil codes.
+__global__ void tcode_kernel(const uint32_t *__restrict__ code, int nx, int ny, int nz, int px, int py, int pz,
+                             uint32_t *__restrict__ tcode) {
+    const int per[3] = {px, py, pz};
+    const int n[3] = {nx, ny, nz};
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int co[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long long)nx * ny))};
+        const uint32_t w = code[c];
+        uint32_t t[2] = {0u, 0u};
+        for (int d = 0; d < 3; ++d) {
+            if (!(w & (uint32_t)node_bit(d))) continue;
+            for (int i = 0; i < 3; ++i) {
+                if (i == d) continue;
+                const int sh = code_shift(d, i);
+                uint32_t slot = (w >> sh) & 3u;
+                for (int m = -2; m <= 2; ++m) {
+                    if (m == 0) continue;
+                    int q[3] = {co[0], co[1], co[2]};
+                    q[i] = nb_coord(q[i] + m, n[i], per[i]);
+                    if (q[i] < 0) continue;  // outside a wall: no node
+                    const uint32_t wb = code[(long long)q[0] + (long long)nx * ((long long)q[1] + (long long)ny * q[2])];
+                    if (!(wb & (uint32_t)node_bit(d))) continue;
+                    const uint32_t k3 = (wb >> sh) & 7u, kind = k3 & 3u;
+                    if (m == -1) slot |= kind << 2;
+                    if (m == 1) slot |= kind << 4;
+                    if (m == -2 && kind == 2u && (k3 & 4u)) slot |= 64u;
+                    if (m == 2 && kind == 2u && !(k3 & 4u)) slot |= 128u;
+                }
+                const int s = tslot(d, i);
+                t[s / 4] |= slot << (8 * (s % 4));
+            }
+        }
+        tcode[2 * c] = t[0];
+        tcode[2 * c + 1] = t[1];
     }
 }
 
@@ -471,6 +525,29 @@ __global__ void sensitivity_kernel(const SensArgs<T> A, int nx, int ny, int nz, 
             }
         }
         out[c] = (float)(scale * s);
+    }
+}
+
+// FP64 block sums of the three velocity components of one state (partials[blk][0..2],
+// [3] = 0), for the mean velocity of fields handed over by the caller.
+template <typename T>
+__global__ void sum_u_kernel(const T *__restrict__ u, long long N, double *__restrict__ partials) {
+    double a[3] = {0.0, 0.0, 0.0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        for (int d = 0; d < 3; ++d) a[d] += (double)u[d * N + c];
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    __shared__ double red[8][3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) red[warp][k] = a[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        if (threadIdx.x < 3)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = s;
     }
 }
 

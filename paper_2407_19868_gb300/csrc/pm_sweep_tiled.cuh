@@ -61,6 +61,9 @@ using Tile64x12c2 = TileCfg<64, 12, 2, 5, 2>;  // 384 threads, 2 CTAs / SM
 using Tile64x12c4 = TileCfg<64, 12, 4, 5, 2>;  // 192 threads, 2 CTAs / SM
 using Tile64x8c4 = TileCfg<64, 8, 4, 4, 3>;    // 128 threads, 3 CTAs / SM
 constexpr int kNumTiles = 3;
+// the transposed sweep (more registers: one CTA per SM), shape index kTileTR
+using Tile64x12c4tr = TileCfg<64, 12, 4, 5, 1>;
+constexpr int kTileTR = 3;
 // FP64 fields use the first shape only.
 template <typename T>
 inline int tile_count() {
@@ -104,6 +107,7 @@ struct TiledSmem {
     TiledStage<T, C> st[C::STAGES];
     T pn[2][C::PNL];  // index: box index - 2 BX
     WallCoef<T> coef[4];
+    T tA[4], tB[4];   // transposed sweep: off-diagonal (A) and diagonal (B) coefficient per wall kind
 };
 
 // A group of N x-adjacent values, aligned for one vector access of up to 16 bytes.
@@ -158,7 +162,8 @@ __device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
 //   forms p^n on plane t-1 (own cells and the +x / +y halo cells),
 //   updates u on plane t-2 with p^n of planes t-2 and t-1 and writes u^{n+1}, p^n.
 // Every shape does the same arithmetic per cell in the same order (bit-identical fields).
-template <typename T, class C, int MODE, bool REDUCE, bool SRC, bool ALPHA>
+// TR: the transposed viscous operator (adjoint solves), from the transposed stencil codes.
+template <typename T, class C, int MODE, bool REDUCE, bool SRC, bool ALPHA, bool TR = false>
 __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int tiles_x, int tiles_y,
                        long long per_cta, int zchunk) {
@@ -198,6 +203,9 @@ __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
         w.A = kind == 0 ? T(1) : (kind == 1 ? T(4) : (kind == 2 ? T(2) : T(8) / T(3)));
         w.K = kind == 2 ? T(-1) : T(0);
         S.coef[tid] = w;
+        // Appendix B stencils as (A on the nodes at +-1, B on the node itself) per kind
+        S.tA[tid] = kind == 0 ? T(1) : (kind == 2 ? T(2) : (kind == 3 ? T(8) / T(3) : T(0)));
+        S.tB[tid] = kind == 0 ? T(-2) : (kind == 1 ? T(-8) : (kind == 2 ? T(-5) : T(-16) / T(3)));
     }
 
     // Persistent CTAs over columns (a column = one drive on one x-y tile, all planes).
@@ -384,6 +392,26 @@ __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
         const T far = (n & 4u) ? up2 : um2;
         lap = fma(w.K, fma(T(1) / T(5), far, u0), lap);
     };
+    // its transpose from the 8-bit slot of the transposed code: the node's own diagonal
+    // coefficient and the coefficients its neighbours apply to it
+    auto perp_t = [&](T &lap, uint32_t tw, int sh, T um2, T um1, T u0, T up1, T up2) {
+        const uint32_t f = tw >> sh;
+        const T cm2 = (f & 64u) ? T(-1) / T(5) : T(0), cp2 = (f & 128u) ? T(-1) / T(5) : T(0);
+        T acc = S.tB[f & 3u] * u0;
+        acc = fma(S.tA[(f >> 2) & 3u], um1, acc);
+        acc = fma(S.tA[(f >> 4) & 3u], up1, acc);
+        acc = fma(cm2, um2, acc);
+        acc = fma(cp2, up2, acc);
+        lap += acc;
+    };
+    // transposed codes of the own cells, loaded one step ahead of the update that uses them
+    uint32_t tcn[2 * CPT];
+    auto load_tc = [&](int k) {
+#pragma unroll
+        for (int j = 0; j < 2 * CPT; ++j) tcn[j] = 0u;
+        if (TR && k >= m0 && k < m1 && real0) ldv(tcn, B.tcode + 2 * ((long long)k * plane + gin_own));
+    };
+    load_tc(t0 - 2);
 
     T *outx = P.uout + (long long)m0 * plane + gin_own;
     T *outp = P.pout + (long long)m0 * plane + gin_own;
@@ -402,6 +430,12 @@ __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
             int sl = s0 + AHEAD;
             if (sl >= STAGES) sl -= STAGES;
             issue_plane(t + AHEAD, sl);
+        }
+        uint32_t tc[2 * CPT];
+        if (TR) {
+#pragma unroll
+            for (int j = 0; j < 2 * CPT; ++j) tc[j] = tcn[j];
+            load_tc(t - 1);
         }
         const TiledStage<T, C> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
         // z queues of the own cells
@@ -473,8 +507,10 @@ __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
 #pragma unroll
                     for (int j = 0; j < CPT; ++j) {
                         T lap = fma(T(-2), u0[j], ext[j + 3] + ext[j + 1]);
-                        perp(lap, c[j], code_shift(0, 1), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
-                        perp(lap, c[j], code_shift(0, 2), qx[Q0][j], qx[Q1][j], u0[j], qx[Q3][j], qx[Q4][j]);
+                        if constexpr (TR) perp_t(lap, tc[2 * j + tslot(0, 1) / 4], 8 * (tslot(0, 1) % 4), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
+                        else perp(lap, c[j], code_shift(0, 1), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
+                        if constexpr (TR) perp_t(lap, tc[2 * j + tslot(0, 2) / 4], 8 * (tslot(0, 2) % 4), qx[Q0][j], qx[Q1][j], u0[j], qx[Q3][j], qx[Q4][j]);
+                        else perp(lap, c[j], code_shift(0, 2), qx[Q0][j], qx[Q1][j], u0[j], qx[Q3][j], qx[Q4][j]);
                         if (ALPHA) {
                             const long long xr = gidx + j + 1 + (j == CPT - 1 ? exl_off : 0);
                             lap -= T(0.5) * (B.alpha[gidx + j] + B.alpha[xr]) * u0[j];
@@ -504,8 +540,10 @@ __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
 #pragma unroll
                     for (int j = 0; j < CPT; ++j) {
                         T lap = fma(T(-2), u0[j], yp1[j] + ym1[j]);
-                        perp(lap, c[j], code_shift(1, 0), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
-                        perp(lap, c[j], code_shift(1, 2), qy[Q0][j], qy[Q1][j], u0[j], qy[Q3][j], qy[Q4][j]);
+                        if constexpr (TR) perp_t(lap, tc[2 * j + tslot(1, 0) / 4], 8 * (tslot(1, 0) % 4), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
+                        else perp(lap, c[j], code_shift(1, 0), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
+                        if constexpr (TR) perp_t(lap, tc[2 * j + tslot(1, 2) / 4], 8 * (tslot(1, 2) % 4), qy[Q0][j], qy[Q1][j], u0[j], qy[Q3][j], qy[Q4][j]);
+                        else perp(lap, c[j], code_shift(1, 2), qy[Q0][j], qy[Q1][j], u0[j], qy[Q3][j], qy[Q4][j]);
                         if (ALPHA) lap -= T(0.5) * (B.alpha[gidx + j] + B.alpha[gidx + j + ey_off]) * u0[j];
                         T R0 = fma(B.inv_re, lap, P.f[1] - (pny[j] - pn_m[j]));
                         if (SRC) R0 += sy[j];
@@ -536,8 +574,10 @@ __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
 #pragma unroll
                     for (int j = 0; j < CPT; ++j) {
                         T lap = fma(T(-2), u0[j], qz[(kRot + 1 + 2) % 5][j] + qz[(kRot + 1 + 0) % 5][j]);
-                        perp(lap, c[j], code_shift(2, 0), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
-                        perp(lap, c[j], code_shift(2, 1), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
+                        if constexpr (TR) perp_t(lap, tc[2 * j + tslot(2, 0) / 4], 8 * (tslot(2, 0) % 4), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
+                        else perp(lap, c[j], code_shift(2, 0), ext[j], ext[j + 1], ext[j + 2], ext[j + 3], ext[j + 4]);
+                        if constexpr (TR) perp_t(lap, tc[2 * j + tslot(2, 1) / 4], 8 * (tslot(2, 1) % 4), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
+                        else perp(lap, c[j], code_shift(2, 1), ym2[j], ym1[j], u0[j], yp1[j], yp2[j]);
                         if (ALPHA) lap -= T(0.5) * (B.alpha[gidx + j] + B.alpha[g2 + j]) * u0[j];
                         T R0 = fma(B.inv_re, lap, P.f[2] - (pn_new[j] - pn_m[j]));
                         if (SRC) R0 += sz[j];
@@ -671,7 +711,8 @@ inline int tiled_grid_size() {
 template <typename T>
 inline int tile_min_blocks(int tile) {
     if (sizeof(T) != 4) return 1;
-    return tile == 0 ? Tile64x12c2::MINB : (tile == 1 ? Tile64x12c4::MINB : Tile64x8c4::MINB);
+    return tile == 0 ? Tile64x12c2::MINB
+                     : (tile == 1 ? Tile64x12c4::MINB : (tile == 2 ? Tile64x8c4::MINB : Tile64x12c4tr::MINB));
 }
 
 // Launch geometry.  zchunk = 0: persistent CTAs (MINB per SM, whole-column rounds then
@@ -747,7 +788,7 @@ inline long long tiled_max_blocks(int nx, int ny, int nz, int nprob) {
     return g;
 }
 
-template <typename T, class C, int MODE, bool RED, bool SRC, bool ALPHA>
+template <typename T, class C, int MODE, bool RED, bool SRC, bool ALPHA, bool TR = false>
 inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, int tile,
                                   cudaStream_t s) {
     TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk, tile);
@@ -756,7 +797,7 @@ inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, 
         sh.grid = (int)(L.unit_begin + (long long)L.tiles_x * L.tiles_y * ((L.nz + L.zchunk - 1) / L.zchunk));
     }
     const size_t smem = sizeof(TiledSmem<T, C>);
-    auto kern = sweep_tiled_kernel<T, C, MODE, RED, SRC, ALPHA>;
+    auto kern = sweep_tiled_kernel<T, C, MODE, RED, SRC, ALPHA, TR>;
     // the shared-memory attributes are per device: one bit per device and instantiation
     static std::atomic<unsigned long long> attr_set{0};
     const int dev = current_device();
@@ -796,6 +837,22 @@ inline cudaError_t launch_tiled_c(const SweepBatch<T> &B, const uint32_t *code, 
     return launch_tiled_m<T, C, kModeP>(B, code, red, src, zchunk, tile, s);
 }
 
+// Transposed sweep (adjoint solves; drag and reductions as needed, no source term).
+template <typename T, class C>
+inline cudaError_t launch_tiled_tr(const SweepBatch<T> &B, const uint32_t *code, int mode, bool red, int zc,
+                                   int tile, cudaStream_t s) {
+    const bool alpha = B.alpha != nullptr;
+#define PM_TR_LAUNCH(M)                                                                                   \
+    return red ? (alpha ? launch_tiled_t<T, C, M, true, false, true, true>(B, code, zc, tile, s)          \
+                        : launch_tiled_t<T, C, M, true, false, false, true>(B, code, zc, tile, s))        \
+               : (alpha ? launch_tiled_t<T, C, M, false, false, true, true>(B, code, zc, tile, s)         \
+                        : launch_tiled_t<T, C, M, false, false, false, true>(B, code, zc, tile, s));
+    if (mode == kModeU) { PM_TR_LAUNCH(kModeU) }
+    if (mode == kModePU) { PM_TR_LAUNCH(kModePU) }
+    PM_TR_LAUNCH(kModeP)
+#undef PM_TR_LAUNCH
+}
+
 // Per-shape launchers, each compiled in its own translation unit (pm_sweep_*.cu).
 cudaError_t launch_tiled_f32_t0(const SweepBatch<float> &B, const uint32_t *code, int mode, bool red, bool src,
                                 int zchunk, cudaStream_t s);
@@ -805,6 +862,16 @@ cudaError_t launch_tiled_f32_t2(const SweepBatch<float> &B, const uint32_t *code
                                 int zchunk, cudaStream_t s);
 cudaError_t launch_tiled_f64_t0(const SweepBatch<double> &B, const uint32_t *code, int mode, bool red, bool src,
                                 int zchunk, cudaStream_t s);
+cudaError_t launch_tiled_f32_tr(const SweepBatch<float> &B, const uint32_t *code, int mode, bool red, int zchunk,
+                                cudaStream_t s);
+
+// Transposed sweep of FP32 fields (tile shape kTileTR: 64 x 12 cells, four per thread, one
+// CTA per SM).  Returns a pm_status.
+inline int launch_tiled_transposed(const SweepBatch<float> &B, const uint32_t *code, int mode, bool red, int zchunk,
+                                   cudaStream_t s) {
+    const cudaError_t e = launch_tiled_f32_tr(B, code, mode, red, zchunk, s);
+    return e == cudaSuccess ? 0 : (e == cudaErrorMemoryAllocation ? 6 : 7);
+}
 
 // One sweep launch with tile shape `tile` (0: 64 x 12, two cells per thread; 1: 64 x 12,
 // four cells per thread; 2: 64 x 8, four cells per thread); FP64 fields use shape 0 (the

@@ -386,11 +386,12 @@ def _extrude(img: np.ndarray, nz_fluid: int = 4) -> np.ndarray:
 
 
 def clogging_sequence(nx: int = 1536, ny: int = 768, n_states: int = 24, phi0: float = 0.55,
-                      phi_end: float = 0.30, seed: int = 3, nz_fluid: int = 4):
-    """Precipitation stand-in: a disk image at porosity phi0, then ``n_states`` states
-    whose porosities fall linearly to phi_end by Eden growth (a random pore pixel with
-    a solid 4-neighbour turns solid), identical in every fluid layer."""
-    img = disk_cell(nx, ny, 12.0, 30.0, phi0, seed)
+                      phi_end: float = 0.30, seed: int = 3, nz_fluid: int = 4, r_lo: float = 12.0,
+                      r_hi: float = 30.0):
+    """Precipitation stand-in: a disk image (radii U[r_lo, r_hi]) at porosity phi0, then
+    ``n_states`` states whose porosities fall linearly to phi_end by Eden growth (a random
+    pore pixel with a solid 4-neighbour turns solid), identical in every fluid layer."""
+    img = disk_cell(nx, ny, r_lo, r_hi, phi0, seed)
     states = []
     cur = img.copy()
     for s in range(n_states):
@@ -407,10 +408,10 @@ def clogging_sequence(nx: int = 1536, ny: int = 768, n_states: int = 24, phi0: f
     return states
 
 
-def crops(states, n_crops: int = 8, lo: int = 256, hi: int = 1024, seed: int = 100, multiple: int = 4):
+def crops(states, n_crops: int = 8, lo: int = 256, hi: int = 1024, seed: int = 100, multiple: int = 1):
     """Sub-domains of uneven in-plane sizes cut from randomly chosen states; the sizes are
     drawn uniformly in [lo, hi] (capped by the image) and rounded down to a multiple of
-    ``multiple`` voxels."""
+    ``multiple`` voxels (1: any size)."""
     g = rng(seed)
     out = []
     for _ in range(n_crops):

@@ -4,7 +4,7 @@ Calls only ``oracle/`` and the seeded input generators; nothing here touches the
 CUDA library.  Each entry records the mask's SHA-256 so a test can check it is
 comparing the same geometry.
 
-    python tests/golden/make_reference.py config1 config2
+    python tests/golden/make_reference.py config1 config2 config5_192 config3_small_s0 config3_small_s1
 """
 import json
 import os
@@ -33,7 +33,31 @@ def config2():
     return m, (0, 1, 2), 1e-10
 
 
-CONFIGS = {"config1": config1, "config2": config2}
+def config5_192():
+    # 192^3 version of the large-domain generator: periodic Boolean model of spheres, radii
+    # U[15, 25], porosity 0.35, seed 5 (rasterised with torch on the CPU; the GPU gives the
+    # same mask); drive x
+    m, _ = G.boolean_spheres_gpu(192, 15.0, 25.0, 0.35, seed=5, device="cpu")
+    return m.numpy(), (0,), 1e-9
+
+
+def _clogging_small():
+    # downsized precipitation sequence: 192 x 96 disk image, radii U[3, 7.5] (the full
+    # workload's 12 .. 30 scaled by 1/4), porosity 0.55 then 0.45 by Eden growth, 4 fluid
+    # layers between solid layers
+    return G.clogging_sequence(192, 96, n_states=2, phi0=0.55, phi_end=0.45, seed=3, r_lo=3.0, r_hi=7.5)
+
+
+def config3_small_s0():
+    return _clogging_small()[0], (0, 1), 1e-8
+
+
+def config3_small_s1():
+    return _clogging_small()[1], (0, 1), 1e-8
+
+
+CONFIGS = {"config1": config1, "config2": config2, "config5_192": config5_192,
+           "config3_small_s0": config3_small_s0, "config3_small_s1": config3_small_s1}
 
 
 def main(names):
@@ -42,9 +66,15 @@ def main(names):
         mask, dirs, tol = CONFIGS[name]()
         t = time.time()
         dom = oracle.Domain(mask)
+        perc = dom.percolation()
         cols = {}
         for j in dirs:
-            r = dom.solve(j, tol=tol, check_every=100)
+            if not perc[j]:
+                # no fluid path around the domain along j: zero column (Sec. 5.1)
+                cols[str(j)] = {"q": [0.0, 0.0, 0.0], "k_col": [0.0, 0.0, 0.0], "iters": 0, "delta": 0.0,
+                                "err_est": 0.0, "percolates": False}
+                continue
+            r = dom.solve(j, tol=tol, check_every=100, max_iter=4_000_000)
             cols[str(j)] = {"q": r["q"].tolist(), "k_col": (r["q"] / oracle.RE_PAPER).tolist(),
                             "iters": r["iters"], "delta": r["delta"], "err_est": r["err_est"]}
             print(name, j, cols[str(j)], time.time() - t, flush=True)
@@ -59,4 +89,4 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(CONFIGS))
+    main(sys.argv[1:] or ["config1", "config2"])

@@ -118,7 +118,8 @@ def test_fixed_pressure_axis_rejections_before_any_device_work(lib):
     assert L.pm_permeability_tensor(C.byref(px), 1.0, C.byref(o), k, None, None, None) == lib.PM_ERR_UNSUPPORTED
     assert L.pm_iterate_noalloc(C.byref(px), 0, 1.0, C.byref(o), 1, u, p, None) == lib.PM_ERR_UNSUPPORTED
     w = (C.c_double * 9)(*([1.0] + [0.0] * 8))
-    assert L.pm_sensitivity(C.byref(px), None, w, C.byref(o), None, None, None, None) == lib.PM_ERR_UNSUPPORTED
+    assert L.pm_sensitivity(C.byref(px), None, w, C.byref(o), None, None, None, None, 0,
+                            None) == lib.PM_ERR_UNSUPPORTED
     doms = (lib.Domain * 1)(px)
     assert L.pm_batch_ktensor(1, doms, None, C.byref(o), k, None, None, None) == lib.PM_ERR_UNSUPPORTED
     dc = lib.options(precision="dc64")

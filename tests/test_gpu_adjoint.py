@@ -96,24 +96,66 @@ def test_ktensor_autograd(api, oracle_mod, case):
 
 
 @pytest.mark.slow
-def test_config4_foam_directional_fd(api):
+def test_config4_foam_gradients(api):
     """192^3 open-cell foam (periodic Voronoi edges of 150 seeds, strut radius 3,
-    porosity 0.90): the adjoint gradient of k_xx at alpha = 0 against a central finite
-    difference of the forward solves along a random direction v over all pore voxels
-    (single-voxel changes are ~1e-10 of k, below solver noise).  The central difference
-    has an O(h^2) error: measured 6.7e-4, 1.7e-4, 4.2e-5 relative at h = 1e-3, 5e-4,
-    2.5e-4, so h = 2.5e-4 with a 1e-4 tolerance."""
+    porosity 0.90), the configuration's two objectives at alpha = 0:
+    * dk_xx/d alpha against a central difference of the FP64 forward solves along a random
+      direction v over all pore voxels (single-voxel changes are ~1e-10 of k, below solver
+      noise).  The central difference has an O(h^2) error: measured 6.7e-4, 1.7e-4,
+      4.2e-5 relative at h = 1e-3, 5e-4, 2.5e-4, so h = 2.5e-4 with a 1e-4 tolerance.
+    * dk_xy/d alpha (forward drive y, transposed solve along x) against a Richardson-
+      extrapolated central difference, fd(h/2) + (fd(h/2) - fd(h)) / 3, since k_xy is
+      ~1e-2 of k_xx.
+    * the whole FP32 gradient of k_xx (FP32 forward and transposed solves on the tiled
+      kernels) against the FP64 gradient, within 1e-3 of its largest value."""
     mask, _ = G.voronoi_foam(192, 150, 3.0, 0.90, seed=4)
     dm = torch.from_numpy(mask).cuda()
     v = (G.rng(61).random(mask.shape) * (mask == 0)).astype(np.float32)
     vt = torch.from_numpy(v).cuda()
-    h = 2.5e-4
     opts = {"precision": "fp64", "tol": 1e-10}
-    w = np.zeros((3, 3))
-    w[0, 0] = 1.0
-    r = api.sensitivity(dm, w, **opts)
-    directional = float((r["dJ"].double() * vt.double()).sum())
-    Jp = api.sensitivity(dm, w, alpha=h * vt, **opts)["J"]
-    Jm = api.sensitivity(dm, w, alpha=-h * vt, **opts)["J"]
-    fd = (Jp - Jm) / (2 * h)
-    assert directional == pytest.approx(fd, rel=1e-4), (directional, fd)
+    wxx, wxy = np.zeros((3, 3)), np.zeros((3, 3))
+    wxx[0, 0] = 1.0
+    wxy[0, 1] = 1.0
+
+    def fd(w, h):
+        # forward solves of w's columns only (no gradient)
+        Jp = api.sensitivity(dm, w, alpha=h * vt, grad=False, **opts)["J"]
+        Jm = api.sensitivity(dm, w, alpha=-h * vt, grad=False, **opts)["J"]
+        return (Jp - Jm) / (2 * h)
+
+    g64 = api.sensitivity(dm, wxx, **opts)["dJ"].double()
+    directional = float((g64 * vt.double()).sum())
+    assert directional == pytest.approx(fd(wxx, 2.5e-4), rel=1e-4)
+    gxy = api.sensitivity(dm, wxy, **opts)["dJ"].double()
+    directional = float((gxy * vt.double()).sum())
+    f1, f2 = fd(wxy, 1e-3), fd(wxy, 5e-4)
+    rich = f2 + (f2 - f1) / 3.0
+    assert directional == pytest.approx(rich, rel=1e-4), (directional, f1, f2, rich)
+    g32 = api.sensitivity(dm, wxx, precision="fp32", tol=1e-7, max_iter=200000)["dJ"].double()
+    assert float((g32 - g64).abs().max()) <= 1e-3 * float(g64.abs().max())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_forward_fields_handed_over(api, case, precision):
+    """Forward fields kept by one call and handed to the next: the second call solves only
+    the transposed systems and gives the same gradient (the same converged fields)."""
+    mask, alpha, w = case
+    a = torch.from_numpy(alpha).cuda()
+    tol = 1e-12 if precision == "fp64" else 1e-9
+    api.sensitivity(mask, w, alpha=a, precision=precision, tol=tol)  # the shape's tuning runs here
+    full = api.sensitivity(mask, w, alpha=a, precision=precision, tol=tol)
+    f = api.sensitivity(mask, None, alpha=a, precision=precision, tol=tol, keep_fwd=True)
+    part = api.sensitivity(mask, w, alpha=a, precision=precision, tol=tol, fwd=f["fwd"])
+    assert torch.equal(part["dJ"], full["dJ"])
+    np.testing.assert_allclose(part["k_raw"], f["k_raw"], rtol=1e-12, atol=1e-15)
+    assert part["J"] == pytest.approx(full["J"], rel=1e-12)
+
+
+def test_tiled_transposed_sweep_matches_simple_kernel(api, case):
+    """The transposed FP32 solves on the tiled kernel and on the simple kernel (option
+    kernel = 1) reach the same gradient within FP32 accuracy."""
+    mask, alpha, w = case
+    a = torch.from_numpy(alpha).cuda()
+    t = api.sensitivity(mask, w, alpha=a, precision="fp32", tol=1e-9)["dJ"].double()
+    s = api.sensitivity(mask, w, alpha=a, precision="fp32", tol=1e-9, kernel=1)["dJ"].double()
+    assert float((t - s).abs().max()) <= 2e-4 * float(s.abs().max())
