@@ -647,7 +647,7 @@ def main():
     ap.add_argument("--schedule", type=int, default=0,
                     help="sweep schedule: 0 automatic, -1 persistent CTAs, n > 0 chunks of n planes")
     ap.add_argument("--tile", type=int, default=0, help="sweep tile shape: 0 automatic, 1..3 pinned")
-    ap.add_argument("--dc-switch-tol", type=float, default=1e-5,
+    ap.add_argument("--dc-switch-tol", type=float, default=1e-6,
                     help="defect correction: window change at which the plain FP32 phase ends")
     ap.add_argument("--large", type=int, default=0, help="large-domain measurement on an n^3 Boolean pack, then exit")
     ap.add_argument("--large-max-iter", type=int, default=40000)

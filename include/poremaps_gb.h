@@ -168,7 +168,8 @@ typedef struct pm_stats {
 
 /* Fills *opt with the defaults: tol 1e-6, check_every 200, max_iter 2e6,
  * PM_FP32_RED64, dt_safety 0.9, Re 0.01, c2 1.5e6, graphs on, percolation check on,
- * dc_switch_tol 1e-5, dc_max_rounds 8, autotune on. */
+ * dc_switch_tol 1e-6, dc_max_rounds 8, autotune on, tile and schedule automatic, batch
+ * mode. */
 PM_API void pm_default_options(pm_options *opt);
 
 /* Returns the scratch memory that the library's pool keeps between calls on the current

@@ -1750,7 +1750,7 @@ void pm_default_options(pm_options *o) {
     o->c2 = 1.5e6;
     o->use_graph = 1;
     o->check_percolation = 1;
-    o->dc_switch_tol = 1e-5;
+    o->dc_switch_tol = 1e-6;
     o->dc_max_rounds = 8;
     o->kernel = 0;
     o->autotune = 1;

@@ -334,6 +334,15 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             if (sl >= kStages) sl -= kStages;
             issue_plane(t + kAhead, sl);
         }
+        if (SRC && real0 && t >= m0 && t < m1) {
+            // the source of plane t is read two steps (velocity) and one step (pressure)
+            // from now: bring its lines into L2 without holding registers
+            const long long g = (long long)t * plane + gin_own;
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(P.src + g));
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(P.src + N + g));
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(P.src + 2 * N + g));
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(P.src + 3 * N + g));
+        }
         const TiledStage<T> &G0 = S.st[s0], &G1 = S.st[s1], &G2 = S.st[s2];
         // z queues of the own column pair
         qx[kRot % 5] = ld2(&G0.ux[own]);
