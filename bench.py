@@ -387,8 +387,9 @@ def run_large(args):
     N = n ** 3
     n_fluid = int(round(info["porosity"] * N))
     t = time.perf_counter()
-    r = api.solve_direction(mask, 0, fields=False, tol=1e-6, check_every=200, max_iter=args.large_max_iter,
-                            check_percolation=0, precision="fp32")
+    r = api.solve_direction(mask, 0, fields=False, tol=1e-6, check_every=args.check_every,
+                            max_iter=args.large_max_iter, check_percolation=0, precision="fp32",
+                            field_memory=args.field_memory)
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t
     st = r["stats"]
@@ -396,6 +397,7 @@ def run_large(args):
     alg = 32 * N + N / 8
     peak, kind = measured_peaks()
     line = {"workload": f"boolean_spheres_{n}c_r20pm5_phi035", "n": n, "cells": N, "porosity": info["porosity"],
+            "field_memory": ["device", "host (one buffer)", "host (both buffers)"][args.field_memory],
             "spheres": info["spheres"], "generate_s": gen_s, "status": r["status"], "iters": st["iters"],
             "k_xx_vx2": float(r["k_col"][0]), "k_col": [float(v) for v in r["k_col"]], "delta": st["delta"],
             "err_est": st["err_est"], "seconds_to_k": solve_s, "sweep_ms": st["sweep_ms"],
@@ -651,6 +653,8 @@ def main():
                     help="defect correction: window change at which the plain FP32 phase ends")
     ap.add_argument("--large", type=int, default=0, help="large-domain measurement on an n^3 Boolean pack, then exit")
     ap.add_argument("--large-max-iter", type=int, default=40000)
+    ap.add_argument("--field-memory", type=int, default=0,
+                    help="large mode: field buffers in device memory (0) or pinned host memory (1: one, 2: both)")
     ap.add_argument("--sequence", action="store_true", help="batched precipitation-sequence measurement, then exit")
     ap.add_argument("--ellipsoid", action="store_true", help="rotated-ellipsoid anisotropy benchmark, then exit")
     ap.add_argument("--thin", action="store_true", help="thin porous media (cylinder cells) benchmark, then exit")

@@ -135,7 +135,16 @@ typedef struct pm_options {
     int32_t sequence;         /* pm_batch_ktensor: 0 = every (domain, drive) problem in each
                                  sweep launch; 1 = the domains in order, each starting from
                                  the converged fields of the previous one (same size) */
-    int32_t reserved[4];
+    int32_t field_memory;     /* where the ping-pong field buffers live: 0 = device memory;
+                                 1 = the second buffer of each drive in pinned host memory,
+                                 2 = both buffers there.  The kernels read and write host
+                                 memory directly (over NVLink-C2C on a Grace CPU), so a
+                                 domain whose fields do not fit device memory can be solved;
+                                 device memory then holds the stencil codes and flags (5 B
+                                 per cell) plus, with 1, one FP32 buffer (16 B per cell and
+                                 drive).  Same fields, bit for bit; slower by the ratio of
+                                 the link's bandwidth to the device memory's. */
+    int32_t reserved[3];
 } pm_options;
 
 typedef struct pm_stats {

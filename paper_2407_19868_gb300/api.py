@@ -61,7 +61,7 @@ class Options(C.Structure):
                 ("c2", C.c_double), ("use_graph", C.c_int32), ("check_percolation", C.c_int32),
                 ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
                 ("autotune", C.c_int32), ("schedule", C.c_int32), ("tile", C.c_int32),
-                ("sequence", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("sequence", C.c_int32), ("field_memory", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class Stats(C.Structure):

@@ -89,13 +89,40 @@ int library_pool(cudaMemPool_t *out) {
 }
 
 // Stream-ordered scratch from the library pool, freed (back into the pool) when the
-// owner goes out of scope.
+// owner goes out of scope; pinned host buffers (fields placed in host memory) are freed
+// after the stream has finished with them.
 struct Scratch {
     cudaStream_t s = nullptr;
-    std::vector<void *> ptrs;
+    std::vector<void *> ptrs, host;
     explicit Scratch(cudaStream_t st) : s(st) {}
     ~Scratch() {
         for (void *p : ptrs) cudaFreeAsync(p, s);
+        if (!host.empty()) {
+            cudaStreamSynchronize(s);
+            for (void *p : host) cudaFreeHost(p);
+        }
+    }
+    // zero-filled buffer in pinned host memory that kernels read and write directly
+    // (over NVLink-C2C on a Grace CPU, PCIe elsewhere)
+    template <typename T>
+    int alloc_host(T **p, size_t count) {
+        *p = nullptr;
+        void *v = nullptr;
+        cudaError_t e = cudaHostAlloc(&v, count * sizeof(T) + 16, cudaHostAllocPortable | cudaHostAllocMapped);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return PM_ERR_OOM;
+        }
+        std::memset(v, 0, count * sizeof(T) + 16);
+        host.push_back(v);
+        void *d = nullptr;
+        e = cudaHostGetDevicePointer(&d, v, 0);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return map_cuda(e);
+        }
+        *p = static_cast<T *>(d);
+        return PM_OK;
     }
     template <typename T>
     int alloc(T **p, size_t count) {
@@ -241,6 +268,7 @@ int validate_options(const pm_options *o) {
     if (!(o->dt_safety > 0) || !(o->Re > 0) || !(o->c2 > 0)) return PM_ERR_INVALID_ARG;
     if (o->schedule < -1) return PM_ERR_INVALID_ARG;
     if (o->tile < 0 || o->tile > kNumTiles) return PM_ERR_INVALID_ARG;
+    if (o->field_memory < 0 || o->field_memory > 2 || o->sequence < 0 || o->sequence > 1) return PM_ERR_INVALID_ARG;
     return PM_OK;
 }
 
@@ -576,6 +604,13 @@ struct Solver {
         for (int k = 0; k < nprob; ++k) {
             const long long Nk = G(k).N;
             for (int b = 0; b < 2; ++b) {
+                // field placement: device memory, or pinned host memory for buffer 1
+                // (field_memory 1) or both buffers (2) -- domains beyond device memory
+                if (o.field_memory > b) {
+                    if ((st = scr.alloc_host(&F[k].u[b], (size_t)(3 * Nk)))) return st;
+                    if ((st = scr.alloc_host(&F[k].p[b], (size_t)Nk))) return st;
+                    continue;
+                }
                 if ((st = scr.alloc(&F[k].u[b], (size_t)(3 * Nk)))) return st;
                 if ((st = scr.alloc(&F[k].p[b], (size_t)Nk))) return st;
                 PM_CK(cudaMemsetAsync(F[k].u[b], 0, sizeof(T) * 3 * Nk, s));
@@ -634,8 +669,8 @@ struct Solver {
 
     // Copy a caller state (same type, iteration units) into the current buffers.
     int load_state(int k, const T *u, const T *p) {
-        if (u) PM_CK(cudaMemcpyAsync(F[k].u[F[k].cur], u, sizeof(T) * 3 * G(k).N, cudaMemcpyDeviceToDevice, s));
-        if (p) PM_CK(cudaMemcpyAsync(F[k].p[F[k].cur], p, sizeof(T) * G(k).N, cudaMemcpyDeviceToDevice, s));
+        if (u) PM_CK(cudaMemcpyAsync(F[k].u[F[k].cur], u, sizeof(T) * 3 * G(k).N, cudaMemcpyDefault, s));
+        if (p) PM_CK(cudaMemcpyAsync(F[k].p[F[k].cur], p, sizeof(T) * G(k).N, cudaMemcpyDefault, s));
         sanitize_kernel<T><<<launch_grid(G(k).N), 256, 0, s>>>(G(k).flags, G(k).N, F[k].u[F[k].cur], F[k].p[F[k].cur]);
         note_launch();
         PM_CK(cudaGetLastError());
@@ -1095,8 +1130,10 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
                                                                u64[k], p64[k], 1.0 / o.Re, f[0], f[1], f[2], r32[k]);
             note_launch();
             for (int b = 0; b < 2; ++b) {
-                PM_CK(cudaMemsetAsync(S.F[k].u[b], 0, sizeof(float) * 3 * N, S.s));
-                PM_CK(cudaMemsetAsync(S.F[k].p[b], 0, sizeof(float) * N, S.s));
+                // a kernel, not a memset: the buffers may be in host memory (field_memory)
+                fill_zero_kernel<float><<<launch_grid(3 * N), 256, 0, S.s>>>(S.F[k].u[b], 3 * N);
+                fill_zero_kernel<float><<<launch_grid(N), 256, 0, S.s>>>(S.F[k].p[b], N);
+                note_launch(2);
             }
             S.F[k].cur = 0;
             S.src[k] = r32[k];
@@ -1172,8 +1209,8 @@ int iterate_impl(const pm_domain *dom, int dir, double drive, const pm_options *
             if ((st = S.sweep(kModePU, false))) return st;
         if ((st = S.sweep(kModeP, false))) return st;
     }
-    PM_CK(cudaMemcpyAsync(u, S.F[0].u[S.F[0].cur], sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
-    PM_CK(cudaMemcpyAsync(p, S.F[0].p[S.F[0].cur], sizeof(T) * g.N, cudaMemcpyDeviceToDevice, s));
+    PM_CK(cudaMemcpyAsync(u, S.F[0].u[S.F[0].cur], sizeof(T) * 3 * g.N, cudaMemcpyDefault, s));
+    PM_CK(cudaMemcpyAsync(p, S.F[0].p[S.F[0].cur], sizeof(T) * g.N, cudaMemcpyDefault, s));
     return PM_OK;
 }
 
@@ -1505,7 +1542,7 @@ int sensitivity_impl(const pm_domain *dom, const float *alpha, const double w[9]
         args.fwd[j] = F.F[k].u[F.F[k].cur];
         for (int i = 0; i < 3; ++i) kr[3 * i + j] = sf[k].q[i] / o->Re * dx2;
         if (u_fwd && u_fwd[j] && !fwd_given)
-            PM_CK(cudaMemcpyAsync(u_fwd[j], args.fwd[j], sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
+            PM_CK(cudaMemcpyAsync(u_fwd[j], args.fwd[j], sizeof(T) * 3 * g.N, cudaMemcpyDefault, s));
     }
     if (ng > 0) {
         // mean velocities of the handed-over fields (Appendix C columns)
@@ -1690,8 +1727,8 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             if (g.N <= wN) {
                 for (int k = 0; k < np; ++k) {
                     const int j = dirs[k];
-                    PM_CK(cudaMemcpyAsync(wu[j], S.F[k].u[S.F[k].cur], sizeof(T) * 3 * g.N, cudaMemcpyDeviceToDevice, s));
-                    PM_CK(cudaMemcpyAsync(wp[j], S.F[k].p[S.F[k].cur], sizeof(T) * g.N, cudaMemcpyDeviceToDevice, s));
+                    PM_CK(cudaMemcpyAsync(wu[j], S.F[k].u[S.F[k].cur], sizeof(T) * 3 * g.N, cudaMemcpyDefault, s));
+                    PM_CK(cudaMemcpyAsync(wp[j], S.F[k].p[S.F[k].cur], sizeof(T) * g.N, cudaMemcpyDefault, s));
                     warm[j] = true;
                 }
                 for (int j = 0; j < 3; ++j) {

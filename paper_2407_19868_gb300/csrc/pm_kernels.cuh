@@ -599,6 +599,14 @@ __global__ void reduce_ranges_kernel(const double *partials, const ReduceRange *
     }
 }
 
+// x = 0, n elements (also for buffers in host memory, where a memset may not apply).
+template <typename T>
+__global__ void fill_zero_kernel(T *__restrict__ x, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] = T(0);
+}
+
 // y = a * x (type conversion allowed), n elements.
 template <typename TO, typename TI>
 __global__ void scale_copy_kernel(TO *__restrict__ y, const TI *__restrict__ x, double a, long long n) {
