@@ -373,3 +373,26 @@ def test_fields_in_host_memory_bit_identical(api, field_memory):
     b = api.permeability_tensor(mask, tol=1e-9, precision="dc64", field_memory=field_memory)
     assert a["stats"][0]["iters"] == b["stats"][0]["iters"]
     np.testing.assert_array_equal(a["k_raw"], b["k_raw"])
+
+
+@pytest.mark.slow
+def test_large_domain_generator_at_192_against_oracle_reference(api):
+    """The large-domain workload (periodic Boolean model of spheres, radii U[15, 25],
+    porosity 0.35, seed 5) at 192^3, generated on the GPU, in the large-domain launch
+    configuration (one drive, no percolation search), against the oracle's converged k
+    column (tests/golden/make_reference.py, the same mask rasterised on the CPU):
+    defect-corrected to 1e-6 of each component, plain FP32 to 1e-5 of k_xx."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "reference_k.json")))
+    if "config5_192" not in ref:
+        pytest.skip("oracle reference not generated")
+    ref = ref["config5_192"]
+    mask, _ = G.boolean_spheres_gpu(192, 15.0, 25.0, 0.35, seed=5)
+    assert G.mask_sha256(mask.cpu().numpy()) == ref["sha256"]
+    ko = np.array(ref["columns"]["0"]["k_col"])
+    dc = api.solve_direction(mask, 0, fields=False, tol=1e-9, check_percolation=0, precision="dc64")
+    assert dc["status"] == api.PM_OK
+    np.testing.assert_allclose(dc["k_col"], ko, rtol=1e-6)
+    fp = api.solve_direction(mask, 0, fields=False, tol=1e-7, check_percolation=0, precision="fp32")
+    assert fp["k_col"][0] == pytest.approx(ko[0], rel=1e-5)
