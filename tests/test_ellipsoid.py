@@ -81,3 +81,48 @@ def test_ellipsoid_anisotropy_ratio_of_the_paper():
     assert r["status"] == api.PM_OK
     k = np.asarray(r["k"])
     assert 2.43 < k[2, 2] / k[1, 1] < 2.53
+
+
+def _gpu_api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():  # pragma: no cover
+        pytest.skip("no CUDA device")
+    from paper_2407_19868_gb300 import api
+    return api, torch
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("ny,frame", [(4, 0), (9, 2)], ids=["uniform", "framed"])
+def test_thin_medium_cell_matches_oracle(oracle_mod, ny, frame):
+    """Thin porous medium of Sec. 6 at a small scale: one cylinder (radius 7 of a 20-voxel
+    cell) across e2, uniform along e2 or between 2-voxel solid frames; k_11 of the GPU
+    solve (defect-corrected) against the oracle's converged value, and the uniform cell's
+    k_22 along the cylinder axis."""
+    api, torch = _gpu_api()
+    m = G.cylinder_cell(20, 7.0, ny, frame)
+    dirs = (0, 1) if frame == 0 else (0,)
+    for j in dirs:
+        r = api.solve_direction(torch.from_numpy(m).cuda(), j, fields=False, precision="dc64", tol=1e-10)
+        q = oracle_mod.Domain(m).solve(j, tol=1e-12, check_every=200)["q"] / oracle_mod.RE_PAPER
+        assert r["k_col"][j] == pytest.approx(q[j], rel=1e-7)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["sc", "bcc", "fcc"])
+def test_regular_pack_matches_oracle_and_kozeny_carman(oracle_mod, kind):
+    """Regular sphere packings of Sec. 6 in a 24-voxel unit cell at porosity 0.45: the full
+    tensor against the oracle's (each component, defect-corrected), cubic isotropy, and
+    the loose Kozeny-Carman agreement the section describes (k_11 within a factor of 2 of
+    D^2 phi^3 / (180 (1 - phi)^2))."""
+    api, torch = _gpu_api()
+    m, rad = G.regular_pack(24, kind, 0.45)
+    _, k_ref, _ = oracle_mod.ktensor(m, tol=1e-12, check_every=200)
+    r = api.permeability_tensor(torch.from_numpy(m).cuda(), precision="dc64", tol=1e-10)
+    k = np.asarray(r["k_raw"])
+    kd = np.mean(np.diag(k_ref))
+    np.testing.assert_allclose(np.diag(k), np.diag(k_ref), rtol=1e-7)
+    assert np.max(np.abs(k - k_ref)) < 1e-7 * kd
+    assert np.max(np.abs(np.diag(k) - kd)) < 1e-6 * kd  # cubic lattice: isotropic
+    phi = float(1 - m.mean())
+    kc = (2 * rad) ** 2 * phi ** 3 / (180.0 * (1 - phi) ** 2)
+    assert 0.5 < k[0, 0] / kc < 2.0
