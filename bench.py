@@ -281,6 +281,22 @@ def run_ours(args):
             ep = k_errors(k_plain, kref)
             plain["k_err_per_component"] = ep.tolist()
             plain["k_err_max"] = float(ep.max())
+    # the adjoint form: the forward solve of drive x and the transposed solve along x, then
+    # dk_xx/d alpha for every voxel (FP32 fields on the tiled kernels, the plain criterion);
+    # the second of two runs, so that the tuning of the shapes is excluded
+    adjoint = None
+    if rank == 0 and args.adjoint:
+        w = np.zeros((3, 3))
+        w[0, 0] = 1.0
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ra = api.sensitivity(dmask, w, precision="fp32", tol=PLAIN_TOL, check_every=args.check_every)
+            torch.cuda.synchronize()
+            adj_s = time.perf_counter() - t
+        adjoint = {"form": "forward drive x + transposed solve along x, dk_xx/d alpha per voxel (FP32, tiled)",
+                   "tol": PLAIN_TOL, "seconds": adj_s, "k_xx": float(ra["k_raw"][0, 0]),
+                   "vs_plain_tensor": adj_s / plain["seconds_to_k_tensor"] if plain else None}
     if kref is not None and ref["sha256"] == G.mask_sha256(mask):
         err = k_errors(results[-1]["k_raw"], kref)
         accuracy = {"reference": "FP64 CPU oracle, window criterion %g (tests/golden/reference_k.json)" % ref["tol"],
@@ -337,6 +353,7 @@ def run_ours(args):
         "k_tensor": [[float(v) for v in row] for row in k],
         "accuracy": accuracy,
         "plain_form": plain,
+        "adjoint_form": adjoint,
         "roofline": {"bound": "hbm", "achieved": top["achieved"], "peak": peak, "unit": "GB/s",
                      "frac": top["frac"], "traffic": stored_traffic(top["alg_bytes_per_launch"]),
                      "peak_kind": peak_kind, "kernel": top["kernel"], "sweep_ms": top["sweep_ms"],
@@ -358,14 +375,15 @@ def run_ours(args):
 def run_profile_case(args):
     """A short run in the benchmark's launch configuration for ncu captures: the same
     mask, three drives batched per sweep launch, FP32 fields, stopped after
-    ``--profile-iters`` iterations (windows of 2 sweeps)."""
+    ``--profile-iters`` iterations (windows of 2 sweeps); with --profile-precision dc64
+    one correction round of as many sweeps follows (the source-carrying sweeps)."""
     import torch
     from paper_2407_19868_gb300 import api
     api.load()
     mask, _ = make_mask()
     r = api.permeability_tensor(torch.from_numpy(mask).cuda(), tol=1e-12, check_every=2,
-                                max_iter=args.profile_iters, precision="fp32", autotune=args.autotune,
-                                schedule=args.schedule)
+                                max_iter=args.profile_iters, precision=args.profile_precision,
+                                autotune=args.autotune, schedule=args.schedule, tile=args.tile, dc_max_rounds=1)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": "pm_permeability_tensor", "iters": r["stats"][0]["iters"],
                       "schedule": r["stats"][0]["schedule"], "status": r["status"]}))
@@ -565,8 +583,11 @@ def run_compare(args):
 def run_sequence(args):
     """Precipitation-sequence measurement: a 1536 x 768 disk image (radii 12..30, porosity
     0.55), 24 states of random solid growth to porosity 0.30, extruded to 4 fluid layers
-    between solid walls, plus 8 crops of uneven sizes; drives x and y of every domain in
-    one batched solve (pm_batch_ktensor, FP32 fields)."""
+    between solid walls, plus 8 crops of uneven sizes; drives x and y of every domain
+    (pm_batch_ktensor, FP32 fields, the paper's criterion 1e-6).  Mode "batch": every
+    (domain, drive) problem in each sweep launch, cold start; mode "sequence": the 24 states
+    in order, each from the converged fields of the one before.  Iterations are capped
+    (--seq-max-iter per problem); the line reports which problems converged."""
     import torch
     from paper_2407_19868_gb300 import api, geometry as G
     api.load()
@@ -574,34 +595,36 @@ def run_sequence(args):
     states = G.clogging_sequence()
     doms = states + G.crops(states)
     gen_s = time.perf_counter() - t
-    dmasks = [torch.from_numpy(m).cuda() for m in doms]
-    res = []
-    for max_iter in (201, args.seq_max_iter):  # a short warm-up, then the measured run
+    modes = ["batch", "sequence"] if args.seq_mode == "both" else [args.seq_mode]
+    for mode in modes:
+        ds = doms if mode == "batch" else states
+        dmasks = [torch.from_numpy(m).cuda() for m in ds]
+        # a short solve first: the tile autotuner runs once per shape outside the timing
+        api.batch_ktensor(dmasks[:1], drives=[3], tol=args.tol, precision="fp32", max_iter=401)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        r = api.batch_ktensor(dmasks, drives=[3] * len(doms), tol=args.tol, precision="fp32",
-                              max_iter=max_iter)
+        r = api.batch_ktensor(dmasks, drives=[3] * len(ds), tol=args.tol, precision="fp32",
+                              max_iter=args.seq_max_iter, sequence=1 if mode == "sequence" else 0)
         torch.cuda.synchronize()
-        res.append((time.perf_counter() - t, r))
-    secs, r = res[-1]
-    cells = sum(m.size for m in doms)
-    fluid = [int(np.count_nonzero(m == 0)) for m in doms]
-    upd = sum(fluid[d] * r["stats"][d][j]["iters"] for d in range(len(doms)) for j in range(2)
-              if r["stats"][d][j]["percolates"])
-    line = {"workload": "clogging_sequence_1536x768x6_24states_8crops", "domains": len(doms), "cells": cells,
-            "generate_s": gen_s, "status": r["status"], "seconds_all_k": secs, "fluid_voxel_updates_per_s": upd / secs,
-            "problems": sum(1 for d in range(len(doms)) for j in range(2) if r["stats"][d][j]["percolates"]),
-            "iters": [[r["stats"][d][j]["iters"] for j in range(2)] for d in range(len(doms))],
-            "converged": [[r["stats"][d][j]["percolates"] and r["stats"][d][j]["status"] == 0 for j in range(2)]
-                          for d in range(len(doms))],
-            "percolates": [[bool(r["stats"][d][j]["percolates"]) for j in range(2)] for d in range(len(doms))],
-            "delta": [[r["stats"][d][j]["delta"] for j in range(2)] for d in range(len(doms))],
-            "max_iter": args.seq_max_iter,
-            "sweep_ms": r["stats"][0][0]["sweep_ms"],
-            "k_xx": [float(r["k"][d][0, 0]) for d in range(len(doms))],
-            "k_yy": [float(r["k"][d][1, 1]) for d in range(len(doms))],
-            "porosity_2d": [float(np.count_nonzero(m[1:-1] == 0)) / m[1:-1].size for m in doms]}
-    print(json.dumps(line), flush=True)
+        secs = time.perf_counter() - t
+        fluid = [int(np.count_nonzero(m == 0)) for m in ds]
+        prob = [(d, j) for d in range(len(ds)) for j in range(2) if r["stats"][d][j]["percolates"]]
+        upd = sum(fluid[d] * r["stats"][d][j]["iters"] for d, j in prob)
+        line = {"workload": "clogging_sequence_1536x768x6_24states" + ("_8crops" if mode == "batch" else ""),
+                "mode": mode, "domains": len(ds), "cells": int(sum(m.size for m in ds)), "generate_s": gen_s,
+                "status": r["status"], "seconds_all_k": secs, "fluid_voxel_updates_per_s": upd / secs,
+                "problems": len(prob),
+                "converged": sum(1 for d, j in prob if r["stats"][d][j]["status"] == 0),
+                "max_iter": args.seq_max_iter, "tol": args.tol,
+                "iters": [[r["stats"][d][j]["iters"] for j in range(2)] for d in range(len(ds))],
+                "percolates": [[bool(r["stats"][d][j]["percolates"]) for j in range(2)] for d in range(len(ds))],
+                "delta": [[r["stats"][d][j]["delta"] for j in range(2)] for d in range(len(ds))],
+                "sweep_ms": r["stats"][0][0]["sweep_ms"], "tile": r["stats"][0][0]["tile"],
+                "k_xx": [float(r["k"][d][0, 0]) for d in range(len(ds))],
+                "k_yy": [float(r["k"][d][1, 1]) for d in range(len(ds))],
+                "shape": [list(m.shape) for m in ds],
+                "porosity_2d": [float(np.count_nonzero(m[1:-1] == 0)) / m[1:-1].size for m in ds]}
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -641,6 +664,7 @@ def main():
     ap.add_argument("--tol", type=float, default=TOL)
     ap.add_argument("--precision", default=PRECISION, choices=["fp32", "dc64", "fp64"])
     ap.add_argument("--plain", type=int, default=1, help="also time the plain FP32 form once (rank 0)")
+    ap.add_argument("--adjoint", type=int, default=1, help="also time the adjoint form once (rank 0)")
     ap.add_argument("--check-every", type=int, default=200)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=300)
@@ -661,7 +685,9 @@ def main():
     ap.add_argument("--packs", action="store_true", help="regular SC / BCC / FCC packings benchmark, then exit")
     ap.add_argument("--compare", action="store_true",
                     help="plain / batched / defect-corrected / FP64 / adjoint forms against the oracle, then exit")
-    ap.add_argument("--seq-max-iter", type=int, default=4001)
+    ap.add_argument("--seq-max-iter", type=int, default=400001)
+    ap.add_argument("--seq-mode", default="both", choices=["batch", "sequence", "both"])
+    ap.add_argument("--profile-precision", default="fp32", choices=["fp32", "dc64"])
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling case: this many iterations of the benchmark solve, then exit")
     args = ap.parse_args()
