@@ -267,7 +267,9 @@ PM_API int pm_permeability_tensor(const pm_domain *dom, double drive, const pm_o
  *   doms: host array of n_domains domains sharing the boundary conditions (else
  *   PM_ERR_UNSUPPORTED).  An x extent that is not a multiple of 4 is handled inside: a
  *   periodic x axis is repeated 2 or 4 times (the same discrete problem), a wall x axis
- *   padded with solid columns; k and the statistics refer to the domain as given.
+ *   padded with solid columns; a thin domain (nz <= 16 and ny >= 8 nz) is solved with its
+ *   y and z axes exchanged (the kernel then marches along the long axis; the stencils are
+ *   the same along every axis).  k and the statistics refer to the domain as given.
  *   drives: host, n_domains bit masks (bit j = drive along e_(j+1)), or NULL / 0 for all.
  *   k_out: host, 9 doubles per domain (row-major, symmetrised); k_raw: same, unsymmetrised,
  *   or NULL.  st: host, 3 pm_stats per domain (per drive), or NULL.

@@ -1620,6 +1620,40 @@ int extend_x(const pm_domain *dom, cudaStream_t s, Scratch &scr, pm_domain *out,
     return PM_OK;
 }
 
+// A thin domain (a few cells along z, many along y) is solved with its y and z axes
+// exchanged, so that the tiled kernel marches along the long axis instead of restarting its
+// plane pipeline every few planes.  The discrete operator treats every axis alike (the
+// same stencils along x, y and z), so the exchanged problem is the same problem with k's
+// rows and columns 1 and 2 exchanged.  Returns whether the axes were exchanged; *out then
+// describes the exchanged mask (in scratch).
+int swap_thin_yz(const pm_domain *dom, cudaStream_t s, Scratch &scr, pm_domain *out, bool *swapped) {
+    *out = *dom;
+    *swapped = false;
+    if (!(dom->nz <= 16 && dom->ny >= 8 * dom->nz)) return PM_OK;
+    const long long N = (long long)dom->nx * dom->ny * dom->nz;
+    const uint8_t *src = dom->mask;
+    int st;
+    if (!dom->mask_on_device) {
+        uint8_t *m = nullptr;
+        if ((st = scr.alloc(&m, (size_t)N))) return st;
+        PM_CK(cudaMemcpyAsync(m, dom->mask, (size_t)N, cudaMemcpyHostToDevice, s));
+        src = m;
+    }
+    uint8_t *t = nullptr;
+    if ((st = scr.alloc(&t, (size_t)N))) return st;
+    swap_yz_kernel<<<launch_grid(N), 256, 0, s>>>(src, dom->nx, dom->ny, dom->nz, t);
+    note_launch();
+    PM_CK(cudaGetLastError());
+    out->ny = dom->nz;
+    out->nz = dom->ny;
+    out->bc[1] = dom->bc[2];
+    out->bc[2] = dom->bc[1];
+    out->mask = t;
+    out->mask_on_device = 1;
+    *swapped = true;
+    return PM_OK;
+}
+
 // Many geometries in one solve.  Batch mode: every (domain, drive) problem is a member of
 // each sweep launch (one CTA per column chunk of each), windows are one captured graph,
 // converged problems are switched off through device flags.  Sequence mode
@@ -1633,6 +1667,9 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
     const long long l0 = t_launches;
     std::vector<Geometry> geos((size_t)nd);
     std::vector<double> qscale((size_t)nd, 1.0);
+    std::vector<char> swapped((size_t)nd, 0);
+    // axis a of the solved problem is axis ax(d, a) of domain d
+    auto ax = [&](int d, int a) { return swapped[(size_t)d] && a > 0 ? 3 - a : a; };
     struct Prob {
         int d, j;
     };
@@ -1643,10 +1680,13 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             k_out[9 * d + i] = 0.0;
             if (k_raw) k_raw[9 * d + i] = 0.0;
         }
-        pm_domain ed;
+        pm_domain sd, ed;
+        bool sw = false;
         int rep = 1;
-        int rc = extend_x(&doms[d], s, scr, &ed, &qscale[(size_t)d], &rep);
+        int rc = swap_thin_yz(&doms[d], s, scr, &sd, &sw);
         if (rc) return rc;
+        swapped[(size_t)d] = sw;
+        if ((rc = extend_x(&sd, s, scr, &ed, &qscale[(size_t)d], &rep))) return rc;
         if ((rc = build_geometry(&ed, s, scr, geos[(size_t)d]))) return rc;
         int perc[3] = {1, 1, 1}, wraps[3];
         long long n_pore = 0;
@@ -1656,12 +1696,14 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             for (int a = 0; a < 3; ++a) perc[a] = wraps[a];
         const int want = drives && drives[d] ? drives[d] : 7;
         for (int j = 0; j < 3; ++j) {
+            // j: axis of the solved problem; the domain's axis is ax(d, j)
+            const int jd = ax(d, j);
             if (st) {
-                std::memset(&st[3 * d + j], 0, sizeof(pm_stats));
-                st[3 * d + j].percolates = perc[j];
-                st[3 * d + j].n_fluid = n_pore / rep;
+                std::memset(&st[3 * d + jd], 0, sizeof(pm_stats));
+                st[3 * d + jd].percolates = perc[j];
+                st[3 * d + jd].n_fluid = n_pore / rep;
             }
-            if (!(want & (1 << j))) continue;
+            if (!(want & (1 << jd))) continue;
             if (!perc[j]) {
                 status = PM_ERR_NOT_PERCOLATING;
                 continue;
@@ -1669,22 +1711,25 @@ int batch_impl(int nd, const pm_domain *doms, const int32_t *drives, const pm_op
             probs.push_back({d, j});
         }
     }
-    // k column j of domain d from the converged mean velocities of problem k
+    // k column j of domain d from the converged mean velocities of problem k (j and the
+    // components of q are axes of the solved problem; ax maps them to the domain's)
     auto record = [&](int d, int j, const pm_stats &b) {
         const double dx2 = doms[d].voxel_size * doms[d].voxel_size;
+        const int jd = ax(d, j);
         for (int i = 0; i < 3; ++i) {
+            const int id = ax(d, i);
             const double kij = qscale[(size_t)d] * b.q[i] / o->Re * dx2;  // Appendix C, column j
-            if (k_raw) k_raw[9 * d + 3 * i + j] = kij;
-            k_out[9 * d + 3 * i + j] += 0.5 * kij;
-            k_out[9 * d + 3 * j + i] += 0.5 * kij;
+            if (k_raw) k_raw[9 * d + 3 * id + jd] = kij;
+            k_out[9 * d + 3 * id + jd] += 0.5 * kij;
+            k_out[9 * d + 3 * jd + id] += 0.5 * kij;
         }
         if (st) {
-            const int perc = st[3 * d + j].percolates;
-            const long long nf = st[3 * d + j].n_fluid;
-            st[3 * d + j] = b;
-            for (int i = 0; i < 3; ++i) st[3 * d + j].q[i] *= qscale[(size_t)d];
-            st[3 * d + j].percolates = perc;
-            st[3 * d + j].n_fluid = nf;
+            const int perc = st[3 * d + jd].percolates;
+            const long long nf = st[3 * d + jd].n_fluid;
+            st[3 * d + jd] = b;
+            for (int i = 0; i < 3; ++i) st[3 * d + jd].q[ax(d, i)] = qscale[(size_t)d] * b.q[i];
+            st[3 * d + jd].percolates = perc;
+            st[3 * d + jd].n_fluid = nf;
         }
     };
     if (o->sequence) {

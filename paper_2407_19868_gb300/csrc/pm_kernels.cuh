@@ -70,6 +70,19 @@ __global__ void extend_x_kernel(const uint8_t *__restrict__ in, int nx, int ny, 
     }
 }
 
+// Mask with its y and z axes exchanged: out[y][z][x] = in[z][y][x] (thin domains are
+// solved with the long axis as the one the tiled kernel marches along).
+__global__ void swap_yz_kernel(const uint8_t *__restrict__ in, int nx, int ny, int nz, uint8_t *__restrict__ out) {
+    const long long M = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < M;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx);
+        const long long r = c / nx;
+        const int z = (int)(r % nz), y = (int)(r / nz);  // out index: (y, z, x)
+        out[c] = in[(long long)x + (long long)nx * ((long long)y + (long long)ny * z)];
+    }
+}
+
 // Zero the values on non-fluid faces and solid cells (the invariant every sweep relies
 // on), used on caller-provided starting fields.
 template <typename T>

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         }
         const T p0 = K.pin[e - kPNo];
         const T pn = MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
-        return (K.cd[e - kPNo] & 1u) ? pn : T(0);
+        return pn;  // a solid cell keeps p = 0: its six faces hold 0, so dv = 0 and rp = 0
     };
     // second derivative across the flow (Appendix B) from the 3-bit wall code, added to lap
     auto perp = [&](T &lap, uint32_t cc, int sh, T um2, T um1, T u0, T up1, T up2) {
@@ -351,7 +351,6 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         // own p^n on plane t-1 (kept in registers until after the update of plane t-2)
         Pair<T> pn_new;
         {
-            const Pair<uint32_t> cd = ld2u<T>(&G1.cd[own - kPNo]);
             const Pair<T> pin = ld2(&G1.pin[own - kPNo]);
             const Pair<T> uyd = ld2(&G1.uy[own - kBX - kUYo]);
             const T uxl = G1.ux[own - 1];
@@ -366,12 +365,11 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                     rp1 = r.b;
                 }
             }
-            const bool pore0 = cd.a & 1u, pore1 = cd.b & 1u;
-            pn_new.a = pore0 ? (MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0)) : T(0);
-            pn_new.b = pore1 ? (MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1)) : T(0);
+            // no pore test: a solid cell has six non-fluid faces (exactly 0), so dv = 0, the
+            // source is 0 there and p stays 0
+            pn_new.a = MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0);
+            pn_new.b = MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1);
             if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) {
-                dv0 = pore0 ? dv0 : T(0);
-                dv1 = pore1 ? dv1 : T(0);
                 acc[3] += (double)dv0 * (double)dv0 + (double)dv1 * (double)dv1;
             }
         }
@@ -487,7 +485,6 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][own - 2 * kBX]) = pn_new;
         if (hrow) {
             // the +y halo row as pairs (same arithmetic as press1, 2-wide loads)
-            const Pair<uint32_t> hc = ld2u<T>(&G1.cd[hown - kPNo]);
             const Pair<T> hp = ld2(&G1.pin[hown - kPNo]);
             const Pair<T> hux = ld2(&G1.ux[hown]);
             const T huxl = G1.ux[hown - 1];
@@ -504,8 +501,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                 }
             }
             Pair<T> hn;
-            hn.a = (hc.a & 1u) ? (MODE == kModeU ? hp.a : hp.a - B.dtc2 * (dv0 - rp0)) : T(0);
-            hn.b = (hc.b & 1u) ? (MODE == kModeU ? hp.b : hp.b - B.dtc2 * (dv1 - rp1)) : T(0);
+            hn.a = MODE == kModeU ? hp.a : hp.a - B.dtc2 * (dv0 - rp0);
+            hn.b = MODE == kModeU ? hp.b : hp.b - B.dtc2 * (dv1 - rp1);
             *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][hown - 2 * kBX]) = hn;
         } else if (hcol) {
             S.pn[(t - 1) & 1][hown - 2 * kBX] = press1(G1, G2, hown, t - 1, hg);

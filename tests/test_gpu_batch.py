@@ -119,3 +119,21 @@ def test_clogging_states_against_oracle_reference(api, name):
         np.testing.assert_allclose(r64["k_raw"][0][:2, j], kj[:2], rtol=1e-6)
         assert abs(r64["k_raw"][0][2, j]) <= 1e-12 * abs(kj[j])  # solid layers close z
         assert r32["k_raw"][0][j, j] == pytest.approx(kj[j], rel=2e-5)
+
+
+def test_thin_domains_exchange_axes(api):
+    """A thin domain (6 cells along z, 96 along y) is solved inside the batch with y and z
+    exchanged; its tensor, statistics and percolation flags are the domain's own, equal to
+    its single solve (which marches along z)."""
+    states = G.clogging_sequence(64, 96, n_states=2, phi0=0.6, phi_end=0.5, seed=11, r_lo=3.0, r_hi=6.0)
+    m = states[1]
+    r = api.batch_ktensor([m, states[0]], drives=[3, 7], tol=1e-10, precision="fp64")
+    single = api.permeability_tensor(m, tol=1e-10, precision="fp64")
+    scale = np.abs(np.diag(single["k_raw"])).max()
+    np.testing.assert_allclose(r["k_raw"][0][:, :2], single["k_raw"][:, :2], rtol=0, atol=1e-8 * scale)
+    assert np.all(r["k_raw"][0][:, 2] == 0)  # drive z not requested
+    for j in range(3):
+        assert r["stats"][1][j]["percolates"] == single["stats"][j]["percolates"]
+    assert not r["stats"][1][2]["percolates"]  # the solid layers close z
+    s0 = api.permeability_tensor(states[0], tol=1e-10, precision="fp64")
+    np.testing.assert_allclose(r["k_raw"][1], s0["k_raw"], rtol=0, atol=1e-8 * np.abs(np.diag(s0["k_raw"])).max())
