@@ -1072,7 +1072,9 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
             (src ? st[k].sweep_ms_src : st[k].sweep_ms) = win_sweeps ? win_ms / (double)win_sweeps : 0.0;
             (src ? st[k].sweeps_timed_src : st[k].sweeps_timed) = win_sweeps;
             st[k].seconds = now_s() - t0;
-            st[k].status = status;
+            // a member of a multi-geometry batch that met its criterion is converged even when
+            // others ran into the iteration limit
+            st[k].status = (S.multi && conv_iter[k] >= 0 && status == PM_ERR_NOT_CONVERGED) ? PM_OK : status;
             st[k].schedule = S.use_tiled() && !S.multi ? (S.zchunk > 0 ? S.zchunk : -1) : 0;
             st[k].setup_seconds = S.t_setup;
             st[k].tile = S.use_tiled() ? S.tile + 1 : 0;

@@ -112,7 +112,9 @@ def test_config4_foam_gradients(api):
     dm = torch.from_numpy(mask).cuda()
     v = (G.rng(61).random(mask.shape) * (mask == 0)).astype(np.float32)
     vt = torch.from_numpy(v).cuda()
-    opts = {"precision": "fp64", "tol": 1e-10}
+    # FP64 solves to a window change of 1e-9: their noise in a difference quotient is ~1e-9 / h
+    # of k, far below the 1e-4 tolerance
+    opts = {"precision": "fp64", "tol": 1e-9}
     wxx, wxy = np.zeros((3, 3)), np.zeros((3, 3))
     wxx[0, 0] = 1.0
     wxy[0, 1] = 1.0
