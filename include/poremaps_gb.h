@@ -110,7 +110,10 @@ typedef struct pm_options {
     int32_t precision;        /* PM_FP32_RED64, PM_FP32_DC64 or PM_FP64 */
     double dt_safety;         /* pseudo-time step = dt_safety x stability root (0.9) */
     double Re;                /* Reynolds number (Sec. 4: 0.01) */
-    double c2;                /* squared artificial speed of sound (Sec. 4: 1.5e6) */
+    double c2;                /* squared artificial speed of sound (Sec. 4: 1.5e6).  The
+                                 converged k does not depend on it, the number of
+                                 iterations does: long thin cells converge faster with a
+                                 larger value, compact packs with a smaller one */
     int32_t use_graph;        /* 1: replay each window as a captured CUDA graph */
     int32_t check_percolation;/* 1: percolation search before solving (device union-find
                                  of the pore cells, winding search on the host over the
@@ -118,9 +121,10 @@ typedef struct pm_options {
     double dc_switch_tol;     /* PM_FP32_DC64: leave plain FP32 sweeps at this change */
     int32_t dc_max_rounds;    /* PM_FP32_DC64: maximum correction rounds */
     int32_t kernel;           /* 0 = default sweep kernel, 1 = simple reference kernel */
-    int32_t autotune;         /* 1: time the tiled kernel's schedules on the first sweeps of
-                                 the first solve of a shape and keep the fastest (those
-                                 sweeps are iterations of the solve and are counted) */
+    int32_t autotune;         /* 1: time the tiled kernel's tile shapes and work splits on
+                                 the first sweeps of the first solve of a shape and keep the
+                                 fastest (those sweeps are iterations of the solve and are
+                                 counted); cached per device, precision and sweep variant */
     int32_t schedule;         /* tiled kernel's work split: 0 = automatic (the autotuner's
                                  choice when autotune is set, else persistent CTAs),
                                  -1 = persistent CTAs, n > 0 = one CTA per tile column
