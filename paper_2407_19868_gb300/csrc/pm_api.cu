@@ -306,7 +306,8 @@ int build_geometry(const pm_domain *dom, cudaStream_t s, Scratch &scr, Geometry 
     note_launch(1);
     PM_CK(cudaGetLastError());
     if ((st = scr.alloc(&g.code, (size_t)g.N))) return st;
-    code_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.code);
+    code_kernel<<<launch_grid(g.N), 256, 0, s>>>(dmask, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.pax,
+                                                 g.code);
     note_launch(1);
     PM_CK(cudaGetLastError());
     return PM_OK;
@@ -740,7 +741,8 @@ struct Solver {
     bool use_tiled() const {
         if (multi) return true;  // batches are built only from tiled-kernel shapes
         if (transposed && (sizeof(T) != 4 || !g.tcode)) return false;  // FP64 adjoint: simple kernel
-        return o.kernel == 0 && g.pax < 0 && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
+        // a fixed-pressure axis runs on tile shape 1 only (the pair kernel's reservoir variant)
+        return o.kernel == 0 && (g.pax < 0 || tile == 0) && tiled_supported<T>(g.nx, g.ny, g.nz, nprob);
     }
 
     // One sweep of the given mode; flips the ping-pong buffers.
@@ -823,6 +825,7 @@ struct Solver {
         std::vector<std::pair<int, int>> cand;  // (tile, zchunk)
         for (int t = 0; t < (transposed ? kTileTR + 1 : tile_count<T>()); ++t) {
             if (transposed ? t != kTileTR : (o.tile > 0 && o.tile <= tile_count<T>() && t != o.tile - 1)) continue;
+            if (g.pax >= 0 && t != 0) continue;
             if (multi || o.schedule != 0) {
                 cand.push_back({t, multi ? 0 : zchunk});
                 continue;
@@ -1408,7 +1411,7 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
                                                                           : cudaMemcpyHostToDevice, s));
     classify_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], -1,
                                                    flags);
-    code_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], code);
+    code_kernel<<<launch_grid(N), 256, 0, s>>>(mask, dom->nx, dom->ny, dom->nz, per[0], per[1], per[2], -1, code);
     sanitize_kernel<T><<<launch_grid(N), 256, 0, s>>>(flags, N, u, p);
     PM_CK(cudaGetLastError());
     if (n == 0) return PM_OK;

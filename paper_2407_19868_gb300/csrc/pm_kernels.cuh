@@ -108,15 +108,22 @@ __device__ __forceinline__ bool cell_pore(const uint8_t *mask, int x, int y, int
     return mask[(long long)x + (long long)nx * ((long long)y + (long long)ny * z)] == 0;
 }
 
+// pax >= 0: fixed-pressure axis; its first and last cell layers are reservoirs whose only
+// fluid nodes are those along the axis (no cross flow inside a reservoir), as in
+// classify_kernel.  The axis is not periodic, so a coordinate along it is never wrapped.
 __device__ __forceinline__ bool node_fluid_at(const uint8_t *mask, int d, int x, int y, int z, int nx, int ny,
-                                              int nz, const int per[3]) {
+                                              int nz, const int per[3], int pax = -1) {
     // coordinates may be up to 3 cells outside; wrap / wall handled per axis
     if (!cell_pore(mask, x, y, z, nx, ny, nz, per)) return false;
+    if (pax >= 0 && d != pax) {
+        const int v = pax == 0 ? x : (pax == 1 ? y : z), n = pax == 0 ? nx : (pax == 1 ? ny : nz);
+        if (v == 0 || v == n - 1) return false;
+    }
     return cell_pore(mask, x + (d == 0), y + (d == 1), z + (d == 2), nx, ny, nz, per);
 }
 
 __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, int nz, int px, int py, int pz,
-                            uint32_t *__restrict__ code) {
+                            int pax, uint32_t *__restrict__ code) {
     const int per[3] = {px, py, pz};
     const long long N = (long long)nx * ny * nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
@@ -128,7 +135,7 @@ __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, in
         if (mask[c] == 0) {
             w |= 1u;
             for (int d = 0; d < 3; ++d) {
-                if (!node_fluid_at(mask, d, x, y, z, nx, ny, nz, per)) continue;
+                if (!node_fluid_at(mask, d, x, y, z, nx, ny, nz, per, pax)) continue;
                 w |= (uint32_t)node_bit(d);
                 for (int i = 0; i < 3; ++i) {
                     if (i == d) continue;
@@ -136,7 +143,7 @@ __global__ void code_kernel(const uint8_t *__restrict__ mask, int nx, int ny, in
                     for (int m = -2; m <= 2; ++m) {
                         if (m == 0) continue;
                         F[m + 2] = node_fluid_at(mask, d, x + (i == 0) * m, y + (i == 1) * m, z + (i == 2) * m,
-                                                 nx, ny, nz, per);
+                                                 nx, ny, nz, per, pax);
                     }
                     // Fig. neighborhoodCases / Appendix B
                     uint32_t k;

@@ -105,7 +105,13 @@ __device__ __forceinline__ uint32_t coef_offset(uint32_t c, int sh) {
     return (c >> (sh - lg)) & (3u << lg);
 }
 
-template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA>
+// PRES: fixed-pressure axis B.pres_axis - 1 (single geometry, no source, no drag).  Its
+// first and last cell layers are reservoirs whose pore cells hold the fixed pressures
+// P.pres[0] / P.pres[1] (their cross-flow nodes are non-fluid in the stencil codes), and
+// the axial second difference of the nodes on the inlet face (coordinate 0) and on the
+// outlet face (coordinate n - 2) takes the node itself as its outer neighbour (zero
+// gradient), as in the simple kernel.
+template <typename T, int MODE, bool REDUCE, bool SRC, bool ALPHA, bool PRES = false>
 __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     sweep_tiled_kernel(const SweepBatch<T> B, const uint32_t *__restrict__ code, int tiles_x, int tiles_y,
                        long long per_cta, int zchunk) {
@@ -143,6 +149,10 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         w.K = kind == 2 ? T(-1) : T(0);
         S.coef[tid] = w;
     }
+
+    // fixed-pressure axis and its length (PRES only)
+    const int pax = PRES ? B.pres_axis - 1 : -1;
+    const int npax = pax == 0 ? nx : (pax == 1 ? ny : nz);
 
     // Persistent CTAs over columns (a column = one drive on one x-y tile, all planes).
     // Phase 1: rounds in which CTA b marches whole column r G + b, so that all CTAs are at
@@ -278,6 +288,15 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
     const long long ex1_off = wxp >= 0 ? (long long)wxp - (gx_own + 1) : 0;  // second cell's +x
     const long long ey_off = wyp >= 0 ? ((long long)wyp - gy_own) * nx : 0;
 
+    // PRES: reservoir of the cell at box index e on plane k (0 inlet, 1 outlet, -1 none);
+    // coordinates outside the box along the (non-periodic) axis are no reservoir
+    auto reservoir = [&](int e, int k) -> int {
+        const int v = pax == 0 ? x0 + e % kBX - 4 : (pax == 1 ? y0 + e / kBX - 2 : k);
+        return v == 0 ? 0 : (v == npax - 1 ? 1 : -1);
+    };
+    // p^n of a reservoir cell: its fixed pressure if pore (code bit 0), else 0
+    auto res_p = [&](int r, uint32_t c) -> T { return (c & 1u) ? P.pres[r] : T(0); };
+
     Pair<T> qx[5], qy[5], qz[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) qx[i] = qy[i] = Pair<T>{T(0), T(0)};
@@ -306,6 +325,10 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             if (gz >= 0) rp = P.src[3 * N + (long long)gz * plane + g];
         }
         const T p0 = K.pin[e - kPNo];
+        if (PRES) {
+            const int r = reservoir(e, k);
+            if (r >= 0) return res_p(r, K.cd[e - kPNo]);
+        }
         const T pn = MODE == kModeU ? p0 : p0 - B.dtc2 * (dv - rp);
         return pn;  // a solid cell keeps p = 0: its six faces hold 0, so dv = 0 and rp = 0
     };
@@ -369,6 +392,20 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             // source is 0 there and p stays 0
             pn_new.a = MODE == kModeU ? pin.a : pin.a - B.dtc2 * (dv0 - rp0);
             pn_new.b = MODE == kModeU ? pin.b : pin.b - B.dtc2 * (dv1 - rp1);
+            if (PRES) {
+                const int ra = reservoir(own, t - 1), rb = reservoir(own + 1, t - 1);
+                if (ra >= 0 || rb >= 0) {
+                    const Pair<uint32_t> cc = ld2u<T>(&G1.cd[own - kPNo]);
+                    if (ra >= 0) {
+                        pn_new.a = res_p(ra, cc.a);
+                        dv0 = T(0);  // a reservoir has no continuity residual
+                    }
+                    if (rb >= 0) {
+                        pn_new.b = res_p(rb, cc.b);
+                        dv1 = T(0);
+                    }
+                }
+            }
             if (REDUCE && real0 && t - 1 >= m0 && t - 1 < m1 && MODE != kModeU) {
                 acc[3] += (double)dv0 * (double)dv0 + (double)dv1 * (double)dv1;
             }
@@ -392,8 +429,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                     const Pair<T> L = ld2(&ux[own - 2]), R = ld2(&ux[own + 2]);
                     const Pair<T> ym2 = ld2(&ux[own - 2 * kBX]), ym1 = ld2(&ux[own - kBX]);
                     const Pair<T> yp1 = ld2(&ux[own + kBX]), yp2 = ld2(&ux[own + 2 * kBX]);
-                    T lap0 = fma(T(-2), u0.a, u0.b + L.b);
-                    T lap1 = fma(T(-2), u0.b, R.a + u0.a);
+                    // -x / +x neighbours of the two cells (the pair's own values inside)
+                    T xm0 = L.b, xp0 = u0.b, xm1 = u0.a, xp1 = R.a;
+                    if (PRES && pax == 0) {
+                        // inlet / outlet faces of a fixed-pressure x axis: zero gradient
+                        if (gx_own == 0) xm0 = u0.a;
+                        if (gx_own == nx - 2) xp0 = u0.a;
+                        if (gx_own + 1 == nx - 2) xp1 = u0.b;
+                    }
+                    T lap0 = fma(T(-2), u0.a, xp0 + xm0);
+                    T lap1 = fma(T(-2), u0.b, xp1 + xm1);
                     perp(lap0, c.a, code_shift(0, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
                     perp(lap1, c.b, code_shift(0, 1), ym2.b, ym1.b, u0.b, yp1.b, yp2.b);
                     perp(lap0, c.a, code_shift(0, 2), qx[(kRot + 1 + 0) % 5].a, qx[(kRot + 1 + 1) % 5].a, u0.a, qx[(kRot + 1 + 3) % 5].a, qx[(kRot + 1 + 4) % 5].a);
@@ -418,7 +463,11 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                     const Pair<T> u0 = qy[(kRot + 1 + 2) % 5];
                     const int oy = own - kUYo;
                     const Pair<T> L = ld2(&uy[oy - 2]), R = ld2(&uy[oy + 2]);
-                    const Pair<T> ym1 = ld2(&uy[oy - kBX]), yp1 = ld2(&uy[oy + kBX]);
+                    Pair<T> ym1 = ld2(&uy[oy - kBX]), yp1 = ld2(&uy[oy + kBX]);
+                    if (PRES && pax == 1) {
+                        if (gy_own == 0) ym1 = u0;
+                        if (gy_own == ny - 2) yp1 = u0;
+                    }
                     T lap0 = fma(T(-2), u0.a, yp1.a + ym1.a);
                     T lap1 = fma(T(-2), u0.b, yp1.b + ym1.b);
                     perp(lap0, c.a, code_shift(1, 0), L.a, L.b, u0.a, u0.b, R.a);
@@ -446,8 +495,13 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
                     const Pair<T> L = ld2(&uz[own - 2]), R = ld2(&uz[own + 2]);
                     const Pair<T> ym2 = ld2(&uz[own - 2 * kBX]), ym1 = ld2(&uz[own - kBX]);
                     const Pair<T> yp1 = ld2(&uz[own + kBX]), yp2 = ld2(&uz[own + 2 * kBX]);
-                    T lap0 = fma(T(-2), u0.a, qz[(kRot + 1 + 2) % 5].a + qz[(kRot + 1 + 0) % 5].a);
-                    T lap1 = fma(T(-2), u0.b, qz[(kRot + 1 + 2) % 5].b + qz[(kRot + 1 + 0) % 5].b);
+                    Pair<T> zp1 = qz[(kRot + 1 + 2) % 5], zm1 = qz[(kRot + 1 + 0) % 5];
+                    if (PRES && pax == 2) {
+                        if (m == 0) zm1 = u0;
+                        if (m == nz - 2) zp1 = u0;
+                    }
+                    T lap0 = fma(T(-2), u0.a, zp1.a + zm1.a);
+                    T lap1 = fma(T(-2), u0.b, zp1.b + zm1.b);
                     perp(lap0, c.a, code_shift(2, 0), L.a, L.b, u0.a, u0.b, R.a);
                     perp(lap1, c.b, code_shift(2, 0), L.b, u0.a, u0.b, R.a, R.b);
                     perp(lap0, c.a, code_shift(2, 1), ym2.a, ym1.a, u0.a, yp1.a, yp2.a);
@@ -503,6 +557,14 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
             Pair<T> hn;
             hn.a = MODE == kModeU ? hp.a : hp.a - B.dtc2 * (dv0 - rp0);
             hn.b = MODE == kModeU ? hp.b : hp.b - B.dtc2 * (dv1 - rp1);
+            if (PRES) {
+                const int ra = reservoir(hown, t - 1), rb = reservoir(hown + 1, t - 1);
+                if (ra >= 0 || rb >= 0) {
+                    const Pair<uint32_t> cc = ld2u<T>(&G1.cd[hown - kPNo]);
+                    if (ra >= 0) hn.a = res_p(ra, cc.a);
+                    if (rb >= 0) hn.b = res_p(rb, cc.b);
+                }
+            }
             *reinterpret_cast<Pair<T> *>(&S.pn[(t - 1) & 1][hown - 2 * kBX]) = hn;
         } else if (hcol) {
             S.pn[(t - 1) & 1][hown - 2 * kBX] = press1(G1, G2, hown, t - 1, hg);
@@ -549,7 +611,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
 }
 
 // ------------------------------------------------------------------ launch
-template <typename T, int MODE, bool RED, bool SRC, bool ALPHA>
+template <typename T, int MODE, bool RED, bool SRC, bool ALPHA, bool PRES = false>
 inline cudaError_t launch_pair_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, cudaStream_t s) {
     TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk, 0);
     if (B.multi) {
@@ -557,7 +619,7 @@ inline cudaError_t launch_pair_t(const SweepBatch<T> &B, const uint32_t *code, i
         sh.grid = (int)(L.unit_begin + (long long)L.tiles_x * L.tiles_y * ((L.nz + L.zchunk - 1) / L.zchunk));
     }
     const size_t smem = sizeof(TiledSmem<T>);
-    auto kern = sweep_tiled_kernel<T, MODE, RED, SRC, ALPHA>;
+    auto kern = sweep_tiled_kernel<T, MODE, RED, SRC, ALPHA, PRES>;
     // the shared-memory attributes are per device: one bit per device and instantiation
     static std::atomic<unsigned long long> attr_set{0};
     const int dev = current_device();
@@ -577,6 +639,12 @@ template <typename T, int MODE>
 inline cudaError_t launch_pair_m(const SweepBatch<T> &B, const uint32_t *code, bool red, bool src, int zc,
                                  cudaStream_t s) {
     const bool alpha = B.alpha != nullptr;
+    if (B.pres_axis) {
+        // fixed-pressure axis: single geometry, no source, no drag
+        if (src || alpha || B.multi) return cudaErrorNotSupported;
+        return red ? launch_pair_t<T, MODE, true, false, false, true>(B, code, zc, s)
+                   : launch_pair_t<T, MODE, false, false, false, true>(B, code, zc, s);
+    }
     if (red) {
         if (src) return alpha ? launch_pair_t<T, MODE, true, true, true>(B, code, zc, s)
                               : launch_pair_t<T, MODE, true, true, false>(B, code, zc, s);

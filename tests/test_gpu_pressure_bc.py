@@ -50,6 +50,73 @@ def test_trajectory_matches_oracle(api, oracle_mod, name, make, bc, a, precision
         assert np.all(ug[nf == 0] == 0)
 
 
+# Domains that span several tiles of the tiled kernel (64 x 12 cells per tile) with ragged
+# last tiles, the reservoirs on every kind of tile edge: x pressure (three tile columns, the
+# last 8 wide), y pressure with the outlet reservoir on the +y halo row of the middle tile
+# row (ny = 25) and alone in the last one, z pressure with plane chunks that start and end
+# next to the reservoirs.  (nz, ny, nx) shapes; x extents are multiples of 4.
+TILED = [
+    ("x_tiles", lambda: G.overlapping_spheres((6, 27, 136), 3.0, 0.55, seed=41), (2, 0, 0), 0, 0),
+    ("y_halo_row", lambda: G.overlapping_spheres((7, 25, 72), 3.0, 0.6, seed=42), (0, 2, 1), 1, 0),
+    ("z_chunks", lambda: G.overlapping_spheres((14, 20, 68), 2.5, 0.6, seed=43), (1, 0, 2), 2, 4),
+]
+
+
+@pytest.mark.parametrize("name,make,bc,a,sched", TILED, ids=[c[0] for c in TILED])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_tiled_trajectory_matches_oracle(api, oracle_mod, name, make, bc, a, sched, precision, tol):
+    """The tiled kernel's fixed-pressure variant (tile shape 1) against the oracle after 1,
+    2 and 10 iterations, element by element."""
+    mask = make()
+    assert mask.shape[2] % 4 == 0
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    dom = oracle_mod.Domain(mask, bc=bc)
+    nf, _ = dom.tables()
+    for n in (1, 2, 10):
+        U, p = dom.zeros()
+        dom.iterate(U, p, n, drive_dir=a, dt=api.time_step())
+        u = torch.zeros((3,) + mask.shape, dtype=dt, device="cuda")
+        pg = torch.zeros(mask.shape, dtype=dt, device="cuda")
+        api.iterate(torch.from_numpy(mask).cuda(), u, pg, n, drive_dir=a, bc=bc, precision=precision,
+                    schedule=sched)
+        ug, pgn = u.double().cpu().numpy(), pg.double().cpu().numpy()
+        su, sp = max(np.max(np.abs(U)), 1e-300), max(np.max(np.abs(p)), 1e-300)
+        assert np.max(np.abs(ug - U)) <= tol * su, (n, "u")
+        assert np.max(np.abs(pgn - p)) <= tol * sp, (n, "p")
+        assert np.all(ug[nf == 0] == 0)
+
+
+@pytest.mark.parametrize("name,make,bc,a,sched", TILED, ids=[c[0] for c in TILED])
+def test_tiled_and_simple_kernels_agree(api, name, make, bc, a, sched):
+    """Tiled fixed-pressure sweep against the one-thread-per-cell kernel (kernel=1) over
+    200 FP64 iterations: equal up to rounding order."""
+    mask = torch.from_numpy(make()).cuda()
+    out = []
+    for kernel in (0, 1):
+        u = torch.zeros((3,) + tuple(mask.shape), dtype=torch.float64, device="cuda")
+        p = torch.zeros(tuple(mask.shape), dtype=torch.float64, device="cuda")
+        api.iterate(mask, u, p, 200, drive_dir=a, bc=bc, precision="fp64", kernel=kernel, schedule=sched)
+        out.append((u.cpu().numpy(), p.cpu().numpy()))
+    (u0, p0), (u1, p1) = out
+    assert np.max(np.abs(u0 - u1)) <= 1e-12 * np.max(np.abs(u1))
+    assert np.max(np.abs(p0 - p1)) <= 1e-12 * np.max(np.abs(p1))
+
+
+def test_tiled_converged_k_and_statistics(api, oracle_mod):
+    """Converged k of a multi-tile fixed-pressure domain on the tiled path (the statistics
+    report tile shape 1), against the oracle."""
+    mask = G.overlapping_spheres((8, 14, 72), 2.5, 0.6, seed=44)
+    bc = (2, 0, 0)
+    _, k_raw, _ = oracle_mod.ktensor(mask, bc=bc, tol=1e-13, check_every=100)
+    r = api.solve_direction(torch.from_numpy(mask).cuda(), 0, fields=False, bc=bc, tol=1e-12,
+                            precision="fp64", check_every=100)
+    assert r["status"] == api.PM_OK
+    assert r["stats"]["tile"] == 1
+    assert r["k_col"][0] == pytest.approx(k_raw[0, 0], rel=1e-8)
+    for i in (1, 2):
+        assert abs(r["k_col"][i] - k_raw[i, 0]) <= 1e-8 * k_raw[0, 0]
+
+
 @pytest.mark.parametrize("precision,tol,rel", [("fp64", 1e-12, 1e-8), ("fp32", 1e-8, 1e-5)])
 def test_converged_k_matches_oracle(api, oracle_mod, precision, tol, rel):
     mask = G.overlapping_spheres((10, 9, 16), 2.0, 0.55, seed=35)
