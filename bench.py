@@ -592,6 +592,15 @@ def run_compare(args):
         print(json.dumps({"mode": name, "seconds": secs, "vs_plain": secs / base, "iters_total": iters,
                           "max_rel_err_diag": ed, "max_rel_err_offdiag": eo, "max_err_offdiag_rel_kii": eok,
                           "meets_1e-5_each": bool(ed <= 1e-5 and eo <= 1e-5)}), flush=True)
+    # fixed-pressure inlet/outlet along x on the same mask (another problem: no reference
+    # k): sweep time of the tiled kernel's reservoir variant and of the simple kernel
+    line = {"mode": "fixed_pressure_x_sweep", "iters": 2001}
+    for kernel, key in ((0, "tiled"), (1, "simple")):
+        r = api.solve_direction(d, 0, fields=False, bc=(2, 0, 0), tol=1e-12, check_every=200, max_iter=2001,
+                                precision="fp32", kernel=kernel)
+        line[f"sweep_ms_{key}"] = r["stats"]["sweep_ms"]
+        line[f"k_xx_{key}"] = float(r["k_col"][0])
+    print(json.dumps(line), flush=True)
     return 0
 
 
