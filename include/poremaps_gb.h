@@ -128,7 +128,9 @@ typedef struct pm_options {
     int32_t schedule;         /* tiled kernel's work split: 0 = automatic (the autotuner's
                                  choice when autotune is set, else persistent CTAs),
                                  -1 = persistent CTAs, n > 0 = one CTA per tile column
-                                 and chunk of n planes */
+                                 and chunk of n planes (a pinned n keeps every chunk whole;
+                                 the autotuner may also cut each column's last chunk into
+                                 shorter pieces, reported in pm_stats.schedule_split) */
     int32_t tile;             /* tiled kernel's tile shape: 0 = automatic (the autotuner's
                                  choice when autotune is set, else 1); 1 = 64 x 12 cells,
                                  two per thread; 2 = 64 x 12, four per thread; 3 = 64 x 8,
@@ -148,7 +150,10 @@ typedef struct pm_options {
                                  per cell) plus, with 1, one FP32 buffer (16 B per cell and
                                  drive).  Same fields, bit for bit; slower by the ratio of
                                  the link's bandwidth to the device memory's. */
-    int32_t reserved[3];
+    int32_t schedule_split;   /* with a pinned schedule n > 0: cut the last chunk of planes
+                                 of every tile column into this many shorter pieces (0 or 1
+                                 = none; at most 64).  Same fields, bit for bit. */
+    int32_t reserved[2];
 } pm_options;
 
 typedef struct pm_stats {
@@ -176,7 +181,10 @@ typedef struct pm_stats {
                                  the kernels it holds) */
     int32_t tile;             /* tiled kernel's tile shape used (pm_options.tile numbering;
                                  0 = simple kernel) */
-    int32_t reserved;
+    int32_t schedule_split;   /* with schedule n > 0: the last chunk of planes of every tile
+                                 column was cut into this many shorter pieces, so that the
+                                 work units that start last fill the GPU's last wave of
+                                 blocks (1 = not cut; 0 = no chunked schedule) */
 } pm_stats;
 
 /* Fills *opt with the defaults: tol 1e-6, check_every 200, max_iter 2e6,

@@ -61,7 +61,8 @@ class Options(C.Structure):
                 ("c2", C.c_double), ("use_graph", C.c_int32), ("check_percolation", C.c_int32),
                 ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
                 ("autotune", C.c_int32), ("schedule", C.c_int32), ("tile", C.c_int32),
-                ("sequence", C.c_int32), ("field_memory", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("sequence", C.c_int32), ("field_memory", C.c_int32), ("schedule_split", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class Stats(C.Structure):
@@ -71,7 +72,7 @@ class Stats(C.Structure):
                 ("status", C.c_int32), ("percolates", C.c_int32), ("schedule", C.c_int32),
                 ("setup_seconds", C.c_double), ("n_fluid", C.c_int64), ("sweep_ms_src", C.c_double),
                 ("sweeps_timed_src", C.c_int64), ("kernel_launches", C.c_int64), ("tile", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("schedule_split", C.c_int32)]
 
     def as_dict(self):
         return {"iters": int(self.iters), "q": [float(v) for v in self.q], "delta": float(self.delta),
@@ -82,7 +83,7 @@ class Stats(C.Structure):
                 "schedule": int(self.schedule), "setup_seconds": float(self.setup_seconds),
                 "n_fluid": int(self.n_fluid), "sweep_ms_src": float(self.sweep_ms_src),
                 "sweeps_timed_src": int(self.sweeps_timed_src), "kernel_launches": int(self.kernel_launches),
-                "tile": int(self.tile)}
+                "tile": int(self.tile), "schedule_split": int(self.schedule_split)}
 
 
 _LIB = None

@@ -266,7 +266,7 @@ int validate_options(const pm_options *o) {
     if (!(o->tol > 0) || o->check_every < 1 || o->max_iter < 1) return PM_ERR_INVALID_ARG;
     if (o->precision < PM_FP32_RED64 || o->precision > PM_FP64) return PM_ERR_INVALID_ARG;
     if (!(o->dt_safety > 0) || !(o->Re > 0) || !(o->c2 > 0)) return PM_ERR_INVALID_ARG;
-    if (o->schedule < -1) return PM_ERR_INVALID_ARG;
+    if (o->schedule < -1 || o->schedule_split < 0 || o->schedule_split > 64) return PM_ERR_INVALID_ARG;
     if (o->tile < 0 || o->tile > kNumTiles) return PM_ERR_INVALID_ARG;
     if (o->field_memory < 0 || o->field_memory > 2 || o->sequence < 0 || o->sequence > 1) return PM_ERR_INVALID_ARG;
     return PM_OK;
@@ -554,6 +554,7 @@ struct Solver {
     const T *alpha = nullptr;
     bool transposed = false;  // adjoint solves: transpose of the viscous operator
     int zchunk = 0;           // tiled-kernel schedule (0 = persistent), from the options or tune()
+    int zsplit = 1;           // chunked schedules: sub-chunks of each column's last chunk (tune())
     int tile = 0;             // tiled-kernel tile shape (index), from the options or tune()
     // multi-geometry batch: problem k lives on geometry *geo[k]
     bool multi = false;
@@ -585,11 +586,12 @@ struct Solver {
         dim3 gr = grid();
         nblk = (long long)gr.x * gr.y * g.nz;
         zchunk = o.schedule > 0 ? o.schedule : 0;
+        zsplit = zchunk > 0 && o.schedule_split > 1 ? o.schedule_split : 1;
         tile = o.tile > 0 && o.tile <= tile_count<T>() ? o.tile - 1 : 0;
         long long nblk_t = tiled_max_blocks<T>(g.nx, g.ny, g.nz, np);
         if (zchunk > 0)
             for (int t = 0; t < tile_count<T>(); ++t) {
-                const long long b = tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, zchunk, t);
+                const long long b = tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, zchunk, t, zsplit);
                 nblk_t = b > nblk_t ? b : nblk_t;
             }
         if (transposed) {
@@ -597,8 +599,10 @@ struct Solver {
             int cand[8];
             const int n = tiled_candidates(g.nx, g.ny, g.nz, np, cand, kTileTR);
             for (int i = 0; i < n; ++i)
-                nblk_t = std::max(nblk_t, tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, cand[i], kTileTR));
-            if (zchunk > 0) nblk_t = std::max(nblk_t, tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, zchunk, kTileTR));
+                for (int sp : kSplits)
+                    nblk_t = std::max(nblk_t, tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, cand[i], kTileTR, sp));
+            if (zchunk > 0)
+                nblk_t = std::max(nblk_t, tiled_num_blocks<T>(g.nx, g.ny, g.nz, np, zchunk, kTileTR, zsplit));
         }
         const long long nblk_max = nblk > nblk_t ? nblk : nblk_t;
         int st;
@@ -725,6 +729,7 @@ struct Solver {
         B.multi = multi ? 1 : 0;
         B.active = multi ? active : nullptr;
         B.pres_axis = g.pax + 1;
+        B.zsplit = multi ? 1 : zsplit;
         return B;
     }
 
@@ -773,7 +778,7 @@ struct Solver {
     }
 
     long long reduce_blocks() const {
-        return use_tiled() ? tiled_num_blocks<T>(g.nx, g.ny, g.nz, nprob, zchunk, tile) : nblk;
+        return use_tiled() ? tiled_num_blocks<T>(g.nx, g.ny, g.nz, nprob, zchunk, tile, zsplit) : nblk;
     }
 
     int reduce_to_host_async() {
@@ -799,14 +804,15 @@ struct Solver {
         struct Entry {
             int dev, size;
             std::vector<long long> key;
-            int tile, zchunk;
+            int tile, zchunk, zsplit;
         };
         static std::mutex mu;
         static std::vector<Entry> cache;
         const int dev = current_device();
         bool has_src = false;
         for (int k = 0; k < nprob; ++k) has_src |= src[k] != nullptr;
-        std::vector<long long> key{multi ? 1 : 0, nprob, o.tile, o.schedule, transposed ? 1 : 0, has_src ? 1 : 0};
+        std::vector<long long> key{multi ? 1 : 0, nprob,      o.tile, o.schedule, o.schedule_split,
+                                   transposed ? 1 : 0, has_src ? 1 : 0};
         for (int k = 0; k < (multi ? nprob : 1); ++k) {
             key.push_back(G(k).nx);
             key.push_back(G(k).ny);
@@ -819,20 +825,33 @@ struct Solver {
                     if (multi && e.tile != tile && set_multi_tile(e.tile)) return 0;
                     tile = e.tile;
                     zchunk = e.zchunk;
+                    zsplit = e.zsplit;
                     return 0;
                 }
         }
-        std::vector<std::pair<int, int>> cand;  // (tile, zchunk)
+        struct Cand {
+            int tile, zchunk, zsplit;
+        };
+        std::vector<Cand> cand;
         for (int t = 0; t < (transposed ? kTileTR + 1 : tile_count<T>()); ++t) {
             if (transposed ? t != kTileTR : (o.tile > 0 && o.tile <= tile_count<T>() && t != o.tile - 1)) continue;
             if (g.pax >= 0 && t != 0) continue;
             if (multi || o.schedule != 0) {
-                cand.push_back({t, multi ? 0 : zchunk});
+                cand.push_back({t, multi ? 0 : zchunk, multi ? 1 : zsplit});
                 continue;
             }
             int zc[8];
             const int n = tiled_candidates(g.nx, g.ny, g.nz, nprob, zc, t);
-            for (int i = 0; i < n; ++i) cand.push_back({t, zc[i]});
+            for (int i = 0; i < n; ++i) {
+                cand.push_back({t, zc[i], 1});
+                if (zc[i] == 0) continue;  // persistent CTAs: no chunks
+                int prev = 1;
+                for (int sp : kSplits) {
+                    const int eff = split_last(g.nz, zc[i] < g.nz ? zc[i] : g.nz, sp);
+                    if (eff > prev) cand.push_back({t, zc[i], eff});
+                    prev = eff > prev ? eff : prev;
+                }
+            }
         }
         cudaEvent_t a, b;
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
@@ -840,15 +859,16 @@ struct Solver {
             return 0;
         }
         float best = 1e30f;
-        std::pair<int, int> pick = cand.empty() ? std::make_pair(tile, zchunk) : cand[0];
+        Cand pick = cand.empty() ? Cand{tile, zchunk, zsplit} : cand[0];
         int done = 0;
         for (const auto &c : cand) {
             if (multi) {
-                if (set_multi_tile(c.first)) break;
+                if (set_multi_tile(c.tile)) break;
             } else {
-                tile = c.first;
+                tile = c.tile;
             }
-            zchunk = c.second;
+            zchunk = c.zchunk;
+            zsplit = c.zsplit;
             bool ok = sweep(kModePU, false) == PM_OK && sweep(kModePU, false) == PM_OK;
             cudaEventRecord(a, s);
             for (int r = 0; r < 2 * reps && ok; ++r) ok = sweep(kModePU, false) == PM_OK;
@@ -865,13 +885,14 @@ struct Solver {
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         if (multi) {
-            if (set_multi_tile(pick.first)) return done;
+            if (set_multi_tile(pick.tile)) return done;
         } else {
-            tile = pick.first;
+            tile = pick.tile;
         }
-        zchunk = pick.second;
+        zchunk = pick.zchunk;
+        zsplit = pick.zsplit;
         std::lock_guard<std::mutex> lock(mu);
-        cache.push_back(Entry{dev, (int)sizeof(T), key, tile, zchunk});
+        cache.push_back(Entry{dev, (int)sizeof(T), key, tile, zchunk, zsplit});
         return done;
     }
 
@@ -1081,6 +1102,7 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
             st[k].schedule = S.use_tiled() && !S.multi ? (S.zchunk > 0 ? S.zchunk : -1) : 0;
             st[k].setup_seconds = S.t_setup;
             st[k].tile = S.use_tiled() ? S.tile + 1 : 0;
+            st[k].schedule_split = S.use_tiled() && !S.multi && S.zchunk > 0 ? S.zsplit : 0;
         }
     return status;
 }
@@ -1428,6 +1450,7 @@ int iterate_noalloc_impl(const pm_domain *dom, int dir, double drive, const pm_o
     B.dt = (T)dts;
     B.dtc2 = (T)(dts * o->c2);
     B.nprob = 1;
+    B.zsplit = o->schedule > 0 && o->schedule_split > 1 ? o->schedule_split : 1;
     for (int d = 0; d < 3; ++d) B.prob[0].f[d] = (T)(d == dir ? drive : 0.0);
     // ping-pong between the caller's fields (buffer 0) and the scratch (buffer 1)
     T *ub[2] = {u, u2}, *pb[2] = {p, p2};

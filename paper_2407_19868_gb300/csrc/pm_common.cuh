@@ -97,6 +97,8 @@ struct SweepBatch {
     int multi;             // 1: problems have their own geometry (tiled kernel, one unit per CTA)
     const int *active;     // device, per problem, 0 = skip (converged); nullptr = all active
     int pres_axis;         // fixed-pressure axis + 1 (reservoir layers 0 and n - 1); 0 = none
+    int zsplit;            // chunked tiled schedules: sub-chunks of each column's last plane
+                           // chunk (split_last in pm_sweep_tiled.cuh); 1 = none
     SweepProblem<T> prob[kMaxBatch];
 };
 

@@ -179,9 +179,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
         m1 = min(nz, m0 + zc);
     } else if (zchunk > 0) {
         if (it > 0) break;
-        col = blockIdx.x % C;
-        m0 = (int)(blockIdx.x / C) * zchunk;
-        m1 = min(nz, m0 + zchunk);
+        chunk_unit(blockIdx.x, C, nz, zchunk, split_last(nz, zchunk, B.zsplit), col, m0, m1);
     } else if (it < rounds) {
         col = it * G + blockIdx.x;
         m0 = 0;
@@ -613,7 +611,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? kMinBlocks : 1)
 // ------------------------------------------------------------------ launch
 template <typename T, int MODE, bool RED, bool SRC, bool ALPHA, bool PRES = false>
 inline cudaError_t launch_pair_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, cudaStream_t s) {
-    TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk, 0);
+    TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk, 0, B.zsplit);
     if (B.multi) {
         const SweepProblem<T> &L = B.prob[B.nprob - 1];
         sh.grid = (int)(L.unit_begin + (long long)L.tiles_x * L.tiles_y * ((L.nz + L.zchunk - 1) / L.zchunk));

@@ -64,6 +64,36 @@ constexpr int kNumTiles = 3;
 // the transposed sweep (more registers: one CTA per SM), shape index kTileTR
 using Tile64x12c4tr = TileCfg<64, 12, 4, 5, 1>;
 constexpr int kTileTR = 3;
+// Chunked schedules (zchunk > 0): chunk-major units of one (column, chunk of zchunk planes)
+// per CTA.  The last chunk of every column (planes (K-1) zchunk .. nz-1, K chunks) may be
+// cut into `split` equal sub-chunks: the units that start last are then short and fill
+// the last wave of CTAs instead of leaving slots idle.  split_last() is the number of
+// non-empty sub-chunks for a requested split; chunk_unit() maps unit u to its column and
+// plane range [m0, m1).  The arithmetic per cell does not depend on the split.
+constexpr int kSplits[3] = {1, 2, 4};  // splits the autotuner tries
+__host__ __device__ inline int split_last(int nz, int zchunk, int split) {
+    const int K = (nz + zchunk - 1) / zchunk, len = nz - (K - 1) * zchunk;
+    int S = split < 1 ? 1 : (split > len ? len : split);
+    while (S > 1 && (S - 1) * ((len + S - 1) / S) >= len) --S;
+    return S;
+}
+__host__ __device__ inline void chunk_unit(long long u, long long C, int nz, int zchunk, int S, long long &col,
+                                           int &m0, int &m1) {
+    const int K = (nz + zchunk - 1) / zchunk;
+    const long long full = (long long)(K - 1) * C;
+    if (u < full) {
+        col = u % C;
+        m0 = (int)(u / C) * zchunk;
+        m1 = m0 + zchunk;
+    } else {
+        const long long j = u - full;
+        const int last0 = (K - 1) * zchunk, L = (nz - last0 + S - 1) / S;
+        col = j % C;
+        m0 = last0 + (int)(j / C) * L;
+        m1 = m0 + L < nz ? m0 + L : nz;
+    }
+}
+
 // FP64 fields use the first shape only.
 template <typename T>
 inline int tile_count() {
@@ -233,9 +263,7 @@ __global__ void __launch_bounds__(C::NT, sizeof(T) == 4 ? C::MINB : 1)
         m1 = min(nz, m0 + zc);
     } else if (zchunk > 0) {
         if (it > 0) break;
-        col = blockIdx.x % Cn;
-        m0 = (int)(blockIdx.x / Cn) * zchunk;
-        m1 = min(nz, m0 + zchunk);
+        chunk_unit(blockIdx.x, Cn, nz, zchunk, split_last(nz, zchunk, B.zsplit), col, m0, m1);
     } else if (it < rounds) {
         col = it * G + blockIdx.x;
         m0 = 0;
@@ -716,9 +744,10 @@ inline int tile_min_blocks(int tile) {
 }
 
 // Launch geometry.  zchunk = 0: persistent CTAs (MINB per SM, whole-column rounds then
-// equal plane ranges); zchunk > 0: one CTA per (column, chunk of zchunk planes).
+// equal plane ranges); zchunk > 0: one CTA per (column, chunk of zchunk planes), the last
+// chunk of each column cut into split_last(nz, zchunk, zsplit) sub-chunks.
 template <typename T>
-inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1, int zchunk = 0, int tile = 0) {
+inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1, int zchunk = 0, int tile = 0, int zsplit = 1) {
     TiledShape s;
     const TileDims td = tile_dims(tile);
     s.tiles_x = (nx + td.tx - 1) / td.tx;
@@ -726,7 +755,7 @@ inline TiledShape tiled_shape(int nx, int ny, int nz, int nprob = 1, int zchunk 
     const long long C = (long long)nprob * s.tiles_x * s.tiles_y;
     s.zchunk = zchunk > 0 ? (zchunk < nz ? zchunk : nz) : 0;
     if (s.zchunk > 0) {
-        s.grid = (int)(C * ((nz + s.zchunk - 1) / s.zchunk));
+        s.grid = (int)(C * ((nz + s.zchunk - 1) / s.zchunk - 1 + split_last(nz, s.zchunk, zsplit)));
         s.per_cta = 0;
     } else {
         s.grid = tiled_grid_size() * tile_min_blocks<T>(tile);
@@ -768,8 +797,8 @@ inline bool tiled_supported(int nx, int ny, int nz, int nprob) {
 
 // Number of reduction partials per drive written by one launch (one per CTA).
 template <typename T>
-inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob, int zchunk = 0, int tile = 0) {
-    return tiled_shape<T>(nx, ny, nz, nprob, zchunk, tile).grid;
+inline long long tiled_num_blocks(int nx, int ny, int nz, int nprob, int zchunk = 0, int tile = 0, int zsplit = 1) {
+    return tiled_shape<T>(nx, ny, nz, nprob, zchunk, tile, zsplit).grid;
 }
 
 // Largest grid over the autotuner's candidates of every tile shape (sizes the
@@ -780,10 +809,11 @@ inline long long tiled_max_blocks(int nx, int ny, int nz, int nprob) {
     for (int t = 0; t < tile_count<T>(); ++t) {
         int cand[8];
         const int n = tiled_candidates(nx, ny, nz, nprob, cand, t);
-        for (int i = 0; i < n; ++i) {
-            const long long b = tiled_num_blocks<T>(nx, ny, nz, nprob, cand[i], t);
-            g = b > g ? b : g;
-        }
+        for (int i = 0; i < n; ++i)
+            for (int sp : kSplits) {
+                const long long b = tiled_num_blocks<T>(nx, ny, nz, nprob, cand[i], t, sp);
+                g = b > g ? b : g;
+            }
     }
     return g;
 }
@@ -791,7 +821,7 @@ inline long long tiled_max_blocks(int nx, int ny, int nz, int nprob) {
 template <typename T, class C, int MODE, bool RED, bool SRC, bool ALPHA, bool TR = false>
 inline cudaError_t launch_tiled_t(const SweepBatch<T> &B, const uint32_t *code, int zchunk, int tile,
                                   cudaStream_t s) {
-    TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk, tile);
+    TiledShape sh = B.multi ? TiledShape{} : tiled_shape<T>(B.nx, B.ny, B.nz, B.nprob, zchunk, tile, B.zsplit);
     if (B.multi) {
         const SweepProblem<T> &L = B.prob[B.nprob - 1];
         sh.grid = (int)(L.unit_begin + (long long)L.tiles_x * L.tiles_y * ((L.nz + L.zchunk - 1) / L.zchunk));

@@ -68,9 +68,11 @@ def test_struct_layout_matches_header(lib, tmp_path):
     import subprocess
     fields = {"pm_domain": (lib.Domain, ["nx", "mask", "voxel_size", "bc"]),
               "pm_options": (lib.Options, ["tol", "max_iter", "precision", "c2", "dc_switch_tol", "kernel",
-                                           "autotune", "schedule", "tile", "sequence", "field_memory"]),
+                                           "autotune", "schedule", "tile", "sequence", "field_memory",
+                                           "schedule_split"]),
               "pm_stats": (lib.Stats, ["iters", "q", "sweep_ms", "status", "percolates", "schedule", "setup_seconds",
-                                       "n_fluid", "sweep_ms_src", "kernel_launches", "tile"])}
+                                       "n_fluid", "sweep_ms_src", "kernel_launches", "tile",
+                                       "schedule_split"])}
     src = ["#include <stdio.h>", "#include <stddef.h>", '#include "poremaps_gb.h"', "int main(void){"]
     for st, (_, fs) in fields.items():
         src.append(f'printf("{st} %zu\\n", sizeof({st}));')

@@ -264,6 +264,35 @@ def test_tiles_and_schedules_give_identical_fields(api, tile, schedule, bc):
     assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("schedule,split", [(5, 2), (5, 4), (10, 3), (10, 4), (40, 2), (40, 4), (40, 7)])
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1)], ids=["periodic", "walls_xz"])
+def test_split_last_chunk_gives_identical_fields(api, tile, schedule, split, bc):
+    """Plane chunks whose last chunk per column is cut into shorter pieces (27 planes:
+    chunks of 5 with a last chunk of 2, chunks of 10 with a last one of 7, one chunk of
+    27 cut into up to 7 pieces) give fields bit-identical to the unsplit schedule."""
+    mask = G.overlapping_spheres((27, 19, 72), 3.0, 0.6, seed=21)
+    ref = _gpu_iterate(api, mask, 11, 1, "fp32", bc=bc)
+    got = _gpu_iterate(api, mask, 11, 1, "fp32", bc=bc, schedule=schedule, schedule_split=split, tile=tile)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+
+
+def test_split_last_chunk_fp64_and_reported(api):
+    """FP64 fields with a split last chunk are bit-identical too; a solve reports the
+    split it ran with and converges to the same k."""
+    mask = G.overlapping_spheres((27, 19, 72), 3.0, 0.6, seed=21)
+    ref = _gpu_iterate(api, mask, 7, 0, "fp64")
+    got = _gpu_iterate(api, mask, 7, 0, "fp64", schedule=10, schedule_split=4)
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+    d = torch.from_numpy(mask).cuda()
+    a = api.solve_direction(d, 0, fields=False, tol=1e-7, schedule=10, tile=1)
+    b = api.solve_direction(d, 0, fields=False, tol=1e-7, schedule=10, schedule_split=4, tile=1)
+    assert a["stats"]["schedule_split"] == 1 and b["stats"]["schedule_split"] == 4
+    assert a["stats"]["iters"] == b["stats"]["iters"]
+    # the FP64 block sums group the cells by CTA: equal up to summation order
+    np.testing.assert_allclose(a["k_col"], b["k_col"], rtol=1e-12, atol=1e-14)
+
+
 @pytest.mark.parametrize("tile", [2, 3])
 def test_tiles_with_source_and_drag_terms(api, tile):
     """The source (defect-correction) and drag (adjoint) variants of the wide shapes
