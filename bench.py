@@ -435,7 +435,8 @@ def run_large(args):
             "k_xx_vx2": float(r["k_col"][0]), "k_col": [float(v) for v in r["k_col"]], "delta": st["delta"],
             "err_est": st["err_est"], "seconds_to_k": solve_s, "sweep_ms": st["sweep_ms"],
             "glups": N / sweep_s / 1e9, "fluid_voxel_updates_per_s": n_fluid / sweep_s,
-            "hbm_gbs": alg / sweep_s / 1e9, "hbm_frac": alg / sweep_s / 1e9 / peak, "peak_kind": kind}
+            "hbm_gbs": alg / sweep_s / 1e9, "hbm_frac": alg / sweep_s / 1e9 / peak, "peak_kind": kind,
+            "tile": st["tile"], "schedule": st["schedule"], "schedule_split": st["schedule_split"]}
     print(json.dumps(line), flush=True)
     return 0
 
