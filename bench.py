@@ -220,7 +220,8 @@ def run_ours(args):
     N = mask.size
     dmask = torch.from_numpy(mask).cuda()
     opts = dict(tol=args.tol, precision=args.precision, check_every=args.check_every, autotune=args.autotune,
-                schedule=args.schedule, tile=args.tile, dc_switch_tol=args.dc_switch_tol)
+                schedule=args.schedule, tile=args.tile, dc_switch_tol=args.dc_switch_tol,
+                dc_extrapolate=args.dc_extrapolate)
 
     def barrier():
         if ws > 1:
@@ -359,7 +360,7 @@ def run_ours(args):
                                                             "fp64": "fp64"}[args.precision],
                    "tol": args.tol, "check_every": args.check_every, "iters_per_step": iters,
                    "dc_rounds": last["dc_rounds"], "schedule": last["schedule"], "tile": last["tile"],
-                   "dc_switch_tol": args.dc_switch_tol,
+                   "dc_switch_tol": args.dc_switch_tol, "dc_extrapolate": args.dc_extrapolate,
                    "seconds_to_k_tensor": dev_ms / 1e3 / args.steps,
                    "setup_seconds_per_step": statistics.mean(s["setup_seconds"] for s in st0),
                    "l2": "working set 1.6 GB of fields per sweep > 129 MB L2 (no flush needed)",
@@ -702,6 +703,9 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="sweep tile shape: 0 automatic, 1..3 pinned")
     ap.add_argument("--dc-switch-tol", type=float, default=1e-6,
                     help="defect correction: window change at which the plain FP32 phase ends")
+    ap.add_argument("--dc-extrapolate", type=int, default=0,
+                    help="defect correction: start the first correction solve from the FP32 phase's "
+                         "geometric-tail error estimate (1) or from zero (0)")
     ap.add_argument("--large", type=int, default=0, help="large-domain measurement on an n^3 Boolean pack, then exit")
     ap.add_argument("--large-max-iter", type=int, default=40000)
     ap.add_argument("--field-memory", type=int, default=0,

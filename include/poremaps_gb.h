@@ -153,7 +153,13 @@ typedef struct pm_options {
     int32_t schedule_split;   /* with a pinned schedule n > 0: cut the last chunk of planes
                                  of every tile column into this many shorter pieces (0 or 1
                                  = none; at most 64).  Same fields, bit for bit. */
-    int32_t reserved[2];
+    int32_t dc_extrapolate;   /* PM_FP32_DC64: 1 = start the first correction solve from the
+                                 geometric-tail estimate of the FP32 phase's remaining error
+                                 (its change over the last window times r / (1 - r), r the
+                                 window-to-window ratio of the mean-velocity change; 0 < r
+                                 <= 0.98), 0 = from zero.  The rounds stop by the same test
+                                 either way. */
+    int32_t reserved[1];
 } pm_options;
 
 typedef struct pm_stats {

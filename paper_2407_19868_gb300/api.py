@@ -62,7 +62,7 @@ class Options(C.Structure):
                 ("dc_switch_tol", C.c_double), ("dc_max_rounds", C.c_int32), ("kernel", C.c_int32),
                 ("autotune", C.c_int32), ("schedule", C.c_int32), ("tile", C.c_int32),
                 ("sequence", C.c_int32), ("field_memory", C.c_int32), ("schedule_split", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("dc_extrapolate", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class Stats(C.Structure):

@@ -269,6 +269,7 @@ int validate_options(const pm_options *o) {
     if (o->schedule < -1 || o->schedule_split < 0 || o->schedule_split > 64) return PM_ERR_INVALID_ARG;
     if (o->tile < 0 || o->tile > kNumTiles) return PM_ERR_INVALID_ARG;
     if (o->field_memory < 0 || o->field_memory > 2 || o->sequence < 0 || o->sequence > 1) return PM_ERR_INVALID_ARG;
+    if (o->dc_extrapolate < 0 || o->dc_extrapolate > 1) return PM_ERR_INVALID_ARG;
     return PM_OK;
 }
 
@@ -949,6 +950,10 @@ struct RunCriterion {
     bool stop_on_stall = false;
     long long max_iter = 0;
     bool retune = false;  // run the autotuner again (the sweep variant changed)
+    // if set: before every window, the state of each problem is copied here (the state
+    // one window before the end is then available for an extrapolation)
+    void *prev_u[kMaxBatch] = {};
+    void *prev_p[kMaxBatch] = {};
 };
 
 // Runs the batch to convergence from the loaded state.  Returns a pm_status.
@@ -1003,6 +1008,20 @@ int run_to_convergence(Solver<T> &S, pm_stats *st, double t0, const RunCriterion
         for (int k = 0; k < S.nprob; ++k) S.F[k].cur = cur0;
     }
     while (!done) {
+        if (C.prev_u[0]) {
+            bool ok = true;
+            for (int k = 0; k < S.nprob && ok; ++k) {
+                const long long Nk = S.G(k).N;
+                ok = cudaMemcpyAsync(C.prev_u[k], S.F[k].u[S.F[k].cur], sizeof(T) * 3 * Nk, cudaMemcpyDefault,
+                                     S.s) == cudaSuccess &&
+                     cudaMemcpyAsync(C.prev_p[k], S.F[k].p[S.F[k].cur], sizeof(T) * Nk, cudaMemcpyDefault, S.s) ==
+                         cudaSuccess;
+            }
+            if (!ok) {
+                status = map_cuda(cudaGetLastError());
+                break;
+            }
+        }
         cudaEventRecord(e0, S.s);
         if (use_graph) {
             cudaError_t e = cudaGraphLaunch(exec, S.s);
@@ -1119,7 +1138,24 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
     c1.tol = o.dc_switch_tol > o.tol ? o.dc_switch_tol : o.tol;
     c1.max_iter = o.max_iter;
     c1.stop_on_stall = true;
+    float *prev_u[kMaxBatch] = {}, *prev_p[kMaxBatch] = {};
+    if (o.dc_extrapolate) {
+        int rc0;
+        for (int k = 0; k < S.nprob; ++k) {
+            if ((rc0 = S.scr.alloc(&prev_u[k], 3 * (size_t)N)) || (rc0 = S.scr.alloc(&prev_p[k], (size_t)N)))
+                return rc0;
+            c1.prev_u[k] = prev_u[k];
+            c1.prev_p[k] = prev_p[k];
+        }
+    }
     int status = run_to_convergence<float>(S, st, t0, &c1);
+    // geometric-tail factor r / (1 - r) of each drive's FP32 phase (0: start from zero)
+    double tail[kMaxBatch] = {};
+    if (o.dc_extrapolate)
+        for (int k = 0; k < S.nprob; ++k) {
+            const double f = st[k].delta > 0 ? st[k].err_est / st[k].delta : 0.0;
+            tail[k] = std::isfinite(f) && f > 0 && f <= 49.0 ? f : 0.0;
+        }
     if (status != PM_OK && status != PM_ERR_NOT_CONVERGED) return status;
     long long iters = st[0].iters, timed = 0;
     double ms = 0.0;
@@ -1156,7 +1192,18 @@ int defect_correction(Solver<float> &S, const Geometry &g, pm_stats *st, double 
             residual64_kernel<<<launch_grid(N), 256, 0, S.s>>>(g.flags, g.nx, g.ny, g.nz, g.per[0], g.per[1], g.per[2],
                                                                u64[k], p64[k], 1.0 / o.Re, f[0], f[1], f[2], r32[k]);
             note_launch();
-            for (int b = 0; b < 2; ++b) {
+            // first round with extrapolation: buffer 0 starts from the estimated remaining
+            // error of the FP32 phase (the FP64 master already holds that phase's state)
+            const bool ext = rounds == 1 && tail[k] > 0;
+            if (ext) {
+                const int c = S.F[k].cur;
+                extrapolate_kernel<float><<<launch_grid(3 * N), 256, 0, S.s>>>(S.F[k].u[0], S.F[k].u[c], prev_u[k],
+                                                                              (float)tail[k], 3 * N);
+                extrapolate_kernel<float><<<launch_grid(N), 256, 0, S.s>>>(S.F[k].p[0], S.F[k].p[c], prev_p[k],
+                                                                          (float)tail[k], N);
+                note_launch(2);
+            }
+            for (int b = ext ? 1 : 0; b < 2; ++b) {
                 // a kernel, not a memset: the buffers may be in host memory (field_memory)
                 fill_zero_kernel<float><<<launch_grid(3 * N), 256, 0, S.s>>>(S.F[k].u[b], 3 * N);
                 fill_zero_kernel<float><<<launch_grid(N), 256, 0, S.s>>>(S.F[k].p[b], N);

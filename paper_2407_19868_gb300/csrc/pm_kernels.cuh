@@ -627,6 +627,16 @@ __global__ void fill_zero_kernel(T *__restrict__ x, long long n) {
         x[i] = T(0);
 }
 
+// out = f (cur - prev), n elements (out may alias cur: each element is read before it is
+// written).  Geometric-tail estimate of the remaining error of an iteration from its
+// change over the last window.
+template <typename T>
+__global__ void extrapolate_kernel(T *out, const T *cur, const T *__restrict__ prev, T f, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = f * (cur[i] - prev[i]);
+}
+
 // y = a * x (type conversion allowed), n elements.
 template <typename TO, typename TI>
 __global__ void scale_copy_kernel(TO *__restrict__ y, const TI *__restrict__ x, double a, long long n) {

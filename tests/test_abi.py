@@ -69,7 +69,7 @@ def test_struct_layout_matches_header(lib, tmp_path):
     fields = {"pm_domain": (lib.Domain, ["nx", "mask", "voxel_size", "bc"]),
               "pm_options": (lib.Options, ["tol", "max_iter", "precision", "c2", "dc_switch_tol", "kernel",
                                            "autotune", "schedule", "tile", "sequence", "field_memory",
-                                           "schedule_split"]),
+                                           "schedule_split", "dc_extrapolate"]),
               "pm_stats": (lib.Stats, ["iters", "q", "sweep_ms", "status", "percolates", "schedule", "setup_seconds",
                                        "n_fluid", "sweep_ms_src", "kernel_launches", "tile",
                                        "schedule_split"])}

@@ -331,6 +331,29 @@ def test_defect_correction_on_a_slowly_converging_geometry(api):
     assert rdc["k_col"][0] == pytest.approx(r64["k_col"][0], rel=1e-7)
 
 
+@pytest.mark.parametrize("geo", ["pack", "dilute"])
+def test_defect_correction_from_the_extrapolated_error(api, oracle_mod, geo):
+    """Starting the first correction solve from the FP32 phase's geometric-tail error
+    estimate changes only the starting point: the tensor meets the same criterion and
+    agrees with the oracle (and with the zero start) per component."""
+    if geo == "pack":
+        mask = G.overlapping_spheres((20, 24, 28), 3.0, 0.6, seed=12)
+        _, k_ref, _ = oracle_mod.ktensor(mask, tol=1e-11)
+        a = api.permeability_tensor(mask, tol=1e-9, precision="dc64", dc_extrapolate=0)
+        b = api.permeability_tensor(mask, tol=1e-9, precision="dc64", dc_extrapolate=1)
+        ka, kb = np.asarray(a["k_raw"]), np.asarray(b["k_raw"])
+    else:
+        mask = G.sc_sphere(32, 4.0)
+        k_ref = api.solve_direction(mask, 0, fields=False, precision="fp64", tol=1e-10, check_every=100)["k_col"]
+        a = api.solve_direction(mask, 0, fields=False, precision="dc64", tol=1e-9, check_every=100, dc_extrapolate=0)
+        b = api.solve_direction(mask, 0, fields=False, precision="dc64", tol=1e-9, check_every=100, dc_extrapolate=1)
+        ka, kb = np.asarray(a["k_col"]), np.asarray(b["k_col"])
+    assert a["status"] == api.PM_OK and b["status"] == api.PM_OK
+    scale = np.abs(k_ref).max()
+    np.testing.assert_allclose(kb, k_ref, rtol=0, atol=1e-7 * scale)
+    np.testing.assert_allclose(kb, ka, rtol=0, atol=1e-7 * scale)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("drive_dir", [0, 2])
 def test_config2_full_size_fields_after_21_iterations(api, oracle_mod, drive_dir):
