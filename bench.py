@@ -339,6 +339,7 @@ def run_ours(args):
     for k in kernels:
         k["achieved"] = k["alg_bytes_per_launch"] / (k["sweep_ms"] * 1e-3) / 1e9
         k["frac"] = k["achieved"] / peak
+        k["traffic"] = stored_traffic(k["alg_bytes_per_launch"])
     top = kernels[0]
     kernel_launches = sum(r["stats"][0]["kernel_launches"] for r in results)
 
