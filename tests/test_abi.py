@@ -61,6 +61,11 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert L.pm_permeability_tensor(C.byref(dom), 1.0, C.byref(o), k, None, None, None) == lib.PM_ERR_INVALID_ARG
     o = lib.options(schedule=-2)
     assert L.pm_permeability_tensor(C.byref(dom), 1.0, C.byref(o), k, None, None, None) == lib.PM_ERR_INVALID_ARG
+    for bad_opt in ({"schedule_split": -1}, {"schedule_split": 65}, {"dc_extrapolate": 2}, {"tile": 4},
+                    {"field_memory": 3}, {"sequence": 2}):
+        o = lib.options(**bad_opt)
+        assert L.pm_permeability_tensor(C.byref(dom), 1.0, C.byref(o), k, None, None, None) == \
+            lib.PM_ERR_INVALID_ARG, bad_opt
 
 
 def test_struct_layout_matches_header(lib, tmp_path):
